@@ -1,0 +1,177 @@
+/*
+ * gres.h -- C ABI of libgres: skyline and grid resistance (gres) on one GPU.
+ *
+ * What is computed (Martinenghi, "Parallelizing the Computation of Robustness
+ * for Measuring the Strength of Tuples"):
+ *   - dominance and the skyline Sky(r):  Def. 1 (Sec. 2);
+ *   - the grid projection gproj(t, g), the lowest corner of the grid cell
+ *     holding t:                          Sec. 2;
+ *   - grid resistance gres(t; r), the finest grid at which gproj(t) leaves
+ *     the skyline of gproj(r); 1 if it never leaves: Def. 2 (Sec. 2) and
+ *     Algorithm 1 (Sec. 3.2); gres depends on skyline tuples only (its
+ *     stability, Sec. 3.2), so candidates are the skyline;
+ *   - Grid / Angular / Sliced partitioning:  Sec. 3.1 (used here to group
+ *     candidate tuples into tiles that can be skipped; speed only).
+ *
+ * Fixed point. A relation r is n rows of d attributes, uint32, row-major
+ * (row i at data[i*d .. i*d+d-1]); a value v stands for the real v / 2^B.
+ * A grid is given by its integer cell width delta: a value projects to
+ * floor(v / delta). The paper's g intervals on [0,1) are the width
+ * delta = 2^B / g. A step list is K strictly ascending widths
+ * delta_0 < ... < delta_{K-1} (finest grid first, i.e. the paper's scan
+ * g = g_bar, ..., 2). The result for a skyline tuple is the index k of the
+ * first width at which some tuple's projection dominates its projection, or
+ * K when that never happens (the paper's gres = 1). The paper's value is
+ * delta_k / 2^B (k < K) or 1 (k = K).
+ *
+ * Direction: GRES_MIN = smaller is better (the paper's convention); GRES_MAX
+ * = larger is better (the opposite convention the paper allows). With
+ * GRES_MAX the projection is still floor(v / delta); only comparisons flip.
+ *
+ * Conventions for every call:
+ *   - Ownership: the caller owns every buffer (host or device). The library
+ *     allocates no device memory in these calls; scratch space comes from the
+ *     caller through (d_ws, ws_bytes), sized by gres_workspace_size(). The
+ *     server object (gres_serve_*) owns the device memory it was given a
+ *     budget for and frees it in gres_serve_destroy().
+ *   - Streams: work is queued on the caller's CUDA stream (cudaStream_t
+ *     passed as void*; NULL = legacy default stream). A call returns after
+ *     queueing unless it writes a host count (h_sky_count != NULL), in which
+ *     case it waits for the stream.
+ *   - Results: skyline indices are original row numbers in ascending order;
+ *     d_step_idx[j] is the result of row d_sky_idx[j].
+ *   - Errors: every call returns a gres_status; no C++ exception crosses the
+ *     ABI. gres_last_error() returns a message for the calling thread's last
+ *     failure. GRES_EINVAL: a bad argument (nothing is launched).
+ *     GRES_ECUDA: a CUDA launch or copy failed (the message has the CUDA
+ *     error string). GRES_ETIMEOUT: a bounded device-side wait ran out.
+ *   - Limits: 1 <= d <= 8, 0 <= n < 2^31, 1 <= K <= 2^20.
+ */
+#ifndef GRES_H
+#define GRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRES_OK = 0,
+    GRES_EINVAL = 1,
+    GRES_ENOMEM = 2,
+    GRES_EAGAIN = 3,
+    GRES_ETIMEOUT = 4,
+    GRES_ECUDA = 5,
+    GRES_EINTERNAL = 6
+} gres_status;
+
+typedef enum { GRES_MIN = 0, GRES_MAX = 1 } gres_dir;
+
+/* Candidate grouping for tile skipping (Sec. 3.1). Results never depend on it. */
+typedef enum {
+    GRES_PART_NONE = 0,     /* skyline order as found (ascending row index)            */
+    GRES_PART_GRID = 1,     /* m slices per attribute, p = m^d cells                  */
+    GRES_PART_ANGULAR = 2,  /* m slices per hyperspherical angle, p = m^(d-1) (Eq. 1)  */
+    GRES_PART_SLICED = 3    /* p equal slices of the order on one attribute            */
+} gres_part;
+
+/* Plan for gres_compute. A NULL plan (or zero fields) means: GRID with m
+ * chosen so that m^d is about 256 cells, 1024 representatives, 8 slots. */
+typedef struct {
+    int32_t scheme;       /* gres_part                                                  */
+    int32_t m;            /* GRID / ANGULAR slices per dimension (0: auto)              */
+    int32_t p;            /* SLICED partitions (0: auto = 64)                           */
+    int32_t slice_dim;    /* SLICED attribute (0 .. d-1)                                */
+    int32_t reps;         /* skyline pre-filter representatives, 1..1024 (0: 1024)      */
+    int32_t slots;        /* gres kernel step slots per lane: 4 or 8 (0: 8)             */
+    int32_t flags;        /* GRES_FLAG_*                                                */
+    int32_t reserved;     /* must be 0                                                  */
+} gres_plan_cfg;
+
+/* Count the (candidate, step) dominance tests the gres kernel evaluates into
+ * d_tests (see gres_compute). Slower; for accounting only. */
+#define GRES_FLAG_COUNT_TESTS 1
+
+/* Thread-local message for the calling thread's most recent failed call
+ * ("" if none). The pointer stays valid until the next call on that thread. */
+const char *gres_last_error(void);
+
+/* Library version string. */
+const char *gres_version(void);
+
+/* Bytes of device scratch that sky_compute / gres_compute need for n rows of
+ * d attributes and K steps. Writes *bytes. GRES_EINVAL for out-of-range
+ * arguments. Pure host computation. */
+gres_status gres_workspace_size(int64_t n, int32_t d, int32_t k, size_t *bytes);
+
+/* Skyline of r (Def. 1) by a sort-by-sum pass with block dominance filters.
+ *   d_data       device, n*d uint32, row-major (read only)
+ *   dir          gres_dir
+ *   d_ws         device scratch, >= gres_workspace_size(n, d, 1) bytes,
+ *                256-byte aligned
+ *   d_sky_idx    device, capacity n int64: skyline row numbers, ascending
+ *   d_sky_count  device int64 (may be NULL): the skyline size S
+ *   h_sky_count  host int64 (may be NULL): S; waits for the stream
+ * Duplicated rows do not dominate each other: all copies of a skyline row
+ * are in the skyline. */
+gres_status sky_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,
+                        void *d_ws, size_t ws_bytes,
+                        int64_t *d_sky_idx, int64_t *d_sky_count, int64_t *h_sky_count,
+                        void *stream);
+
+/* Grid resistance of every skyline tuple (Def. 2, Algorithm 1): the skyline
+ * (as sky_compute), then for each skyline tuple t the first step k at which
+ * some skyline tuple's projection dominates t's projection.
+ *   h_steps      host, k uint32 widths, strictly ascending, >= 1
+ *   cfg          plan (may be NULL); see gres_plan_cfg
+ *   d_ws         device scratch, >= gres_workspace_size(n, d, k) bytes
+ *   d_sky_idx    device, capacity n int64: skyline rows, ascending
+ *   d_step_idx   device, capacity n int32: result per skyline row, in [0, k]
+ *   d_sky_count  device int64 (may be NULL): S
+ *   h_sky_count  host int64 (may be NULL): S; waits for the stream
+ *   d_tests      device uint64 (may be NULL): with GRES_FLAG_COUNT_TESTS, the
+ *                number of (candidate, step) tests evaluated, added to *d_tests
+ * With h_sky_count == NULL nothing waits on the host, so the call can be
+ * captured into a CUDA graph (all sizes after the skyline live on the device). */
+gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,
+                         const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
+                         void *d_ws, size_t ws_bytes,
+                         int64_t *d_sky_idx, int32_t *d_step_idx,
+                         int64_t *d_sky_count, int64_t *h_sky_count,
+                         unsigned long long *d_tests, void *stream);
+
+/* Host-buffer form of gres_compute: copies h_data to the device, computes,
+ * and copies the S results back, all on `stream`, then waits for it.
+ *   h_data       host, n*d uint32 row-major (pinned memory copies faster)
+ *   d_ws         device scratch, >= gres_workspace_size_host(n, d, k) bytes
+ *   h_sky_idx    host, capacity n int64
+ *   h_step_idx   host, capacity n int32
+ *   h_sky_count  host int64 (required) */
+gres_status gres_workspace_size_host(int64_t n, int32_t d, int32_t k, size_t *bytes);
+gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int32_t dir,
+                              const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
+                              void *d_ws, size_t ws_bytes,
+                              int64_t *h_sky_idx, int32_t *h_step_idx, int64_t *h_sky_count,
+                              void *stream);
+
+/* Grid projection (Sec. 2) of `count` values at each of k widths:
+ * d_out[j*count + i] = floor(d_values[i] / h_steps[j]) (the paper's
+ * floor(t[i] g) numerator with delta = 2^B / g). Division by a run-time
+ * invariant divisor uses multiply-high constants (Granlund & Montgomery,
+ * PLDI 1994), exact for every uint32 value.
+ *   d_values  device, count uint32;  d_out  device, k*count uint32. */
+gres_status gres_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps,
+                       int32_t k, uint32_t *d_out, void *stream);
+
+/* Host helper: the multiply-high constants gres_gproj uses for divisor
+ * `delta` (>= 1): floor(v / delta) = (t + ((v - t) >> s1)) >> s2 with
+ * t = mulhi(m, v). Exposed so the constants can be checked without a GPU. */
+gres_status gres_udiv_magic(uint32_t delta, uint32_t *m, uint32_t *s1, uint32_t *s2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRES_H */

@@ -1,0 +1,289 @@
+// api.cu -- the extern "C" entry points of libgres (include/gres.h): argument
+// validation, workspace layout, stream handling and error reporting. All
+// computation is queued as CUDA kernels (skyline.cu, radix_sort.cu,
+// gres_stage.cu); nothing here computes a result on the host.
+#include "gres_internal.cuh"
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gres_status fail(gres_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+gres_status cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return GRES_ECUDA;
+}
+
+gres_status check_dims(int64_t n, int32_t d) {
+    if (d < 1 || d > gres::kMaxD) return fail(GRES_EINVAL, "d must be in [1, 8]");
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(GRES_EINVAL, "n must be in [0, 2^31)");
+    return GRES_OK;
+}
+
+gres_status check_steps(const uint32_t *h_steps, int32_t k) {
+    if (k < 1 || k > (1 << 20)) return fail(GRES_EINVAL, "k must be in [1, 2^20]");
+    if (!h_steps) return fail(GRES_EINVAL, "h_steps is NULL");
+    if (h_steps[0] < 1) return fail(GRES_EINVAL, "steps must be >= 1");
+    for (int32_t i = 1; i < k; i++)
+        if (h_steps[i] <= h_steps[i - 1]) return fail(GRES_EINVAL, "steps must be strictly ascending");
+    return GRES_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+gres_status check_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *out) {
+    gres_plan_cfg c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    if (cfg == nullptr) c.scheme = GRES_PART_GRID;
+    if (c.scheme < GRES_PART_NONE || c.scheme > GRES_PART_SLICED)
+        return fail(GRES_EINVAL, "cfg.scheme must be a gres_part");
+    if (c.reserved != 0) return fail(GRES_EINVAL, "cfg.reserved must be 0");
+    if (c.flags & ~GRES_FLAG_COUNT_TESTS) return fail(GRES_EINVAL, "unknown cfg.flags bits");
+    if (c.reps == 0) c.reps = gres::kMaxReps;
+    if (c.reps < 1 || c.reps > gres::kMaxReps) return fail(GRES_EINVAL, "cfg.reps must be in [1, 1024]");
+    if (c.slots == 0) c.slots = 8;
+    if (c.slots != 4 && c.slots != 8) return fail(GRES_EINVAL, "cfg.slots must be 4 or 8");
+    if (c.scheme == GRES_PART_GRID || c.scheme == GRES_PART_ANGULAR) {
+        const int dims = c.scheme == GRES_PART_GRID ? d : d - 1;
+        if (c.m == 0) {
+            // about 256 cells
+            int m = 2;
+            while (dims > 0) {
+                double cells = 1.0;
+                for (int i = 0; i < dims; i++) cells *= (m + 1);
+                if (cells > 256.0 * 1.5) break;
+                m++;
+            }
+            c.m = dims > 0 ? m : 1;
+        }
+        if (c.m < 1) return fail(GRES_EINVAL, "cfg.m must be >= 1");
+        double cells = 1.0;
+        for (int i = 0; i < dims; i++) cells *= c.m;
+        if (cells > 4294967295.0) return fail(GRES_EINVAL, "cfg.m^d must be < 2^32");
+        if (c.scheme == GRES_PART_ANGULAR && c.m > 64) return fail(GRES_EINVAL, "ANGULAR m must be <= 64");
+    }
+    if (c.scheme == GRES_PART_SLICED) {
+        if (c.p == 0) c.p = 64;
+        if (c.p < 1) return fail(GRES_EINVAL, "cfg.p must be >= 1");
+        if (c.slice_dim < 0 || c.slice_dim >= d) return fail(GRES_EINVAL, "cfg.slice_dim must be in [0, d)");
+    }
+    *out = c;
+    return GRES_OK;
+}
+
+bool ws_ok(void *d_ws, size_t ws_bytes, size_t need) {
+    return d_ws != nullptr && ws_bytes >= need && (reinterpret_cast<uintptr_t>(d_ws) & 255u) == 0;
+}
+
+gres_status read_status(gres::Workspace &ws, cudaStream_t st) {
+    unsigned int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, &ws.hdr->status, sizeof(status), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (status & gres::kStatusTimeout) return fail(GRES_ETIMEOUT, "a bounded device wait ran out");
+    if (status & gres::kStatusInternal) return fail(GRES_EINTERNAL, "internal device check failed");
+    return GRES_OK;
+}
+
+gres_status finish_counts(gres::Workspace &ws, int64_t *d_sky_count, int64_t *h_sky_count, cudaStream_t st) {
+    cudaError_t e;
+    if (d_sky_count) {
+        e = cudaMemcpyAsync(d_sky_count, &ws.hdr->n_sky, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "count copy");
+    }
+    if (h_sky_count) {
+        long long s = 0;
+        e = cudaMemcpyAsync(&s, &ws.hdr->n_sky, sizeof(s), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "count copy");
+        gres_status r = read_status(ws, st);
+        if (r != GRES_OK) return r;
+        *h_sky_count = s;
+    }
+    return GRES_OK;
+}
+
+}  // namespace
+
+namespace gres {
+
+size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
+    const int DP = padded_dims(d);
+    const int64_t nn = n > 0 ? n : 1;
+    const int64_t rows_pad = nn + kTileRows;
+    const int64_t tiles = rows_pad / kTileRows + 1;
+    size_t off = 0;
+    char *b = static_cast<char *>(base);
+    auto take = [&](size_t bytes) -> void * {
+        void *p = b ? b + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    Workspace w;
+    w.hdr = static_cast<WsHeader *>(take(sizeof(WsHeader)));
+    w.keys[0] = static_cast<unsigned long long *>(take(8 * nn));
+    w.keys[1] = static_cast<unsigned long long *>(take(8 * nn));
+    w.vals[0] = static_cast<uint32_t *>(take(4 * nn));
+    w.vals[1] = static_cast<uint32_t *>(take(4 * nn));
+    w.hist = static_cast<uint32_t *>(take(4 * 256 * (sort_blocks(nn) + 1)));
+    w.blocksum = static_cast<uint32_t *>(take(4 * (scan_blocks(nn) + 1)));
+    w.flags = static_cast<uint32_t *>(take(4 * nn));
+    w.surv_rows = static_cast<uint32_t *>(take(4 * DP * nn));
+    w.surv_orig = static_cast<uint32_t *>(take(4 * nn));
+    w.reps = static_cast<uint32_t *>(take(4 * DP * kMaxReps));
+    w.sky_rows = static_cast<uint32_t *>(take(4 * DP * rows_pad));
+    w.cand = static_cast<uint32_t *>(take(4 * DP * rows_pad));
+    w.tmin = static_cast<uint32_t *>(take(4 * DP * tiles));
+    w.perm = static_cast<uint32_t *>(take(4 * nn));
+    w.res = static_cast<int32_t *>(take(4 * nn));
+    w.steps = static_cast<uint32_t *>(take(4 * (size_t)(k > 0 ? k : 1)));
+    w.magic = static_cast<uint32_t *>(take(16 * (size_t)(k > 0 ? k : 1)));
+    w.bytes = off;
+    if (ws) *ws = w;
+    return off;
+}
+
+}  // namespace gres
+
+extern "C" {
+
+const char *gres_last_error(void) { return g_last_error.c_str(); }
+
+const char *gres_version(void) { return "libgres 0.1 (sm_103a)"; }
+
+gres_status gres_workspace_size(int64_t n, int32_t d, int32_t k, size_t *bytes) {
+    if (!bytes) return fail(GRES_EINVAL, "bytes is NULL");
+    gres_status s = check_dims(n, d);
+    if (s != GRES_OK) return s;
+    if (k < 1 || k > (1 << 20)) return fail(GRES_EINVAL, "k must be in [1, 2^20]");
+    *bytes = gres::workspace_layout(n, d, k, nullptr, nullptr);
+    return GRES_OK;
+}
+
+gres_status gres_workspace_size_host(int64_t n, int32_t d, int32_t k, size_t *bytes) {
+    gres_status s = gres_workspace_size(n, d, k, bytes);
+    if (s != GRES_OK) return s;
+    const int64_t nn = n > 0 ? n : 1;
+    *bytes += align256(4 * (size_t)nn * d) + align256(8 * (size_t)nn) + align256(4 * (size_t)nn);
+    return GRES_OK;
+}
+
+gres_status sky_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,
+                        void *d_ws, size_t ws_bytes,
+                        int64_t *d_sky_idx, int64_t *d_sky_count, int64_t *h_sky_count,
+                        void *stream) {
+    gres_status s = check_dims(n, d);
+    if (s != GRES_OK) return s;
+    if (dir != GRES_MIN && dir != GRES_MAX) return fail(GRES_EINVAL, "dir must be GRES_MIN or GRES_MAX");
+    if (n > 0 && (!d_data || !d_sky_idx)) return fail(GRES_EINVAL, "d_data / d_sky_idx is NULL");
+    const size_t need = gres::workspace_layout(n, d, 1, nullptr, nullptr);
+    if (!ws_ok(d_ws, ws_bytes, need)) return fail(GRES_EINVAL, "workspace too small, NULL or not 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gres::Workspace ws;
+    gres::workspace_layout(n, d, 1, d_ws, &ws);
+    cudaError_t e = gres::launch_init(ws, n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    e = gres::launch_skyline(d_data, n, d, dir, gres::kMaxReps, ws, d_sky_idx, st);
+    if (e != cudaSuccess) return cuda_fail(e, "skyline");
+    return finish_counts(ws, d_sky_count, h_sky_count, st);
+}
+
+gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,
+                         const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
+                         void *d_ws, size_t ws_bytes,
+                         int64_t *d_sky_idx, int32_t *d_step_idx,
+                         int64_t *d_sky_count, int64_t *h_sky_count,
+                         unsigned long long *d_tests, void *stream) {
+    gres_status s = check_dims(n, d);
+    if (s != GRES_OK) return s;
+    if (dir != GRES_MIN && dir != GRES_MAX) return fail(GRES_EINVAL, "dir must be GRES_MIN or GRES_MAX");
+    s = check_steps(h_steps, k);
+    if (s != GRES_OK) return s;
+    gres_plan_cfg plan;
+    s = check_plan(cfg, d, &plan);
+    if (s != GRES_OK) return s;
+    if (n > 0 && (!d_data || !d_sky_idx || !d_step_idx))
+        return fail(GRES_EINVAL, "d_data / d_sky_idx / d_step_idx is NULL");
+    const size_t need = gres::workspace_layout(n, d, k, nullptr, nullptr);
+    if (!ws_ok(d_ws, ws_bytes, need)) return fail(GRES_EINVAL, "workspace too small, NULL or not 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gres::Workspace ws;
+    gres::workspace_layout(n, d, k, d_ws, &ws);
+    cudaError_t e = gres::launch_init(ws, n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    e = gres::launch_upload_steps(ws, h_steps, k, st);
+    if (e != cudaSuccess) return cuda_fail(e, "steps upload");
+    e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st);
+    if (e != cudaSuccess) return cuda_fail(e, "skyline");
+    e = gres::launch_gres_stage(d_data, n, d, dir, k, plan, ws, d_sky_idx, d_step_idx, d_tests, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gres stage");
+    return finish_counts(ws, d_sky_count, h_sky_count, st);
+}
+
+gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int32_t dir,
+                              const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
+                              void *d_ws, size_t ws_bytes,
+                              int64_t *h_sky_idx, int32_t *h_step_idx, int64_t *h_sky_count,
+                              void *stream) {
+    gres_status s = check_dims(n, d);
+    if (s != GRES_OK) return s;
+    if (!h_sky_count) return fail(GRES_EINVAL, "h_sky_count is NULL");
+    if (n > 0 && (!h_data || !h_sky_idx || !h_step_idx))
+        return fail(GRES_EINVAL, "h_data / h_sky_idx / h_step_idx is NULL");
+    size_t need = 0;
+    s = gres_workspace_size_host(n, d, k > 0 ? k : 1, &need);
+    if (s != GRES_OK) return s;
+    if (!ws_ok(d_ws, ws_bytes, need)) return fail(GRES_EINVAL, "workspace too small, NULL or not 256-byte aligned");
+    const size_t core = gres::workspace_layout(n, d, k, nullptr, nullptr);
+    const int64_t nn = n > 0 ? n : 1;
+    char *extra = static_cast<char *>(d_ws) + core;
+    uint32_t *d_data = reinterpret_cast<uint32_t *>(extra);
+    int64_t *d_sky = reinterpret_cast<int64_t *>(extra + align256(4 * (size_t)nn * d));
+    int32_t *d_res = reinterpret_cast<int32_t *>(extra + align256(4 * (size_t)nn * d) + align256(8 * (size_t)nn));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(d_data, h_data, 4 * (size_t)n * d, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    }
+    int64_t S = 0;
+    s = gres_compute(d_data, n, d, dir, h_steps, k, cfg, d_ws, core, d_sky, d_res, nullptr, &S, nullptr, stream);
+    if (s != GRES_OK) return s;
+    if (S > 0) {
+        cudaError_t e = cudaMemcpyAsync(h_sky_idx, d_sky, 8 * (size_t)S, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "result copy");
+        e = cudaMemcpyAsync(h_step_idx, d_res, 4 * (size_t)S, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "result copy");
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    }
+    *h_sky_count = S;
+    return GRES_OK;
+}
+
+gres_status gres_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps,
+                       int32_t k, uint32_t *d_out, void *stream) {
+    if (count < 0) return fail(GRES_EINVAL, "count must be >= 0");
+    gres_status s = check_steps(h_steps, k);
+    if (s != GRES_OK) return s;
+    if (count > 0 && (!d_values || !d_out)) return fail(GRES_EINVAL, "d_values / d_out is NULL");
+    cudaError_t e = gres::launch_gproj(d_values, count, h_steps, k, d_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "gproj");
+    return GRES_OK;
+}
+
+gres_status gres_udiv_magic(uint32_t delta, uint32_t *m, uint32_t *s1, uint32_t *s2) {
+    if (delta < 1 || !m || !s1 || !s2) return fail(GRES_EINVAL, "delta must be >= 1, outputs non-NULL");
+    gres::udiv_magic(delta, m, s1, s2);
+    return GRES_OK;
+}
+
+}  // extern "C"

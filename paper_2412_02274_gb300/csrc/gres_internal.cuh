@@ -1,0 +1,107 @@
+// gres_internal.cuh -- shared declarations of libgres (device helpers, workspace
+// layout, kernel launchers). Not part of the public ABI (see include/gres.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gres.h"
+
+namespace gres {
+
+constexpr int kMaxD = 8;
+constexpr int kTileRows = 32;          // candidate rows per pruning tile
+constexpr int kMaxReps = 1024;         // skyline pre-filter representatives
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // padding row value: never dominates
+
+// Rows of canonical values are stored padded to DP words (16-byte multiples).
+__host__ __device__ constexpr int padded_dims(int d) { return d <= 4 ? 4 : 8; }
+
+// Status bits written by kernels into the workspace header.
+enum : uint32_t {
+    kStatusTimeout = 1u,   // a bounded device-side wait ran out
+    kStatusInternal = 2u,  // an internal capacity or consistency check failed
+};
+
+// ---------------------------------------------------------------------------
+// Workspace: one caller-owned device buffer, carved into 256-byte aligned
+// regions. The header holds device-side sizes so that nothing after the input
+// size needs the host (the whole call can be captured into a CUDA graph).
+struct WsHeader {
+    unsigned long long key_min;   // key range of the current sort
+    unsigned long long key_max;
+    long long n_rows;             // input rows n
+    long long n_surv;             // rows left after the representative filter
+    long long n_sky;              // skyline size S
+    long long n_reps;             // representatives kept (mutually non-dominated)
+    unsigned int work_next;       // dynamic work counter of the gres kernel
+    unsigned int status;          // kStatus* bits
+    unsigned int sorted_sel;      // buffer (0/1) holding the last radix sort's result
+    unsigned int lo[kMaxD];       // per-attribute canonical minimum over the skyline
+    unsigned int hi[kMaxD];       // per-attribute canonical maximum over the skyline
+    unsigned int pad[11];
+};
+
+// Digit passes that do work in the radix sort of the current key range; the
+// sorted data is in buffer (passes & 1), recorded in sorted_sel once the
+// sort is done.
+__device__ __forceinline__ int radix_passes(const WsHeader *h) {
+    unsigned long long range = h->key_max >= h->key_min ? h->key_max - h->key_min : 0ull;
+    int bits = range ? 64 - __clzll((long long)range) : 0;
+    return (bits + 7) >> 3;
+}
+
+struct Workspace {
+    WsHeader *hdr;
+    unsigned long long *keys[2];  // radix sort key ping-pong, n each
+    uint32_t *vals[2];            // radix sort value ping-pong, n each
+    uint32_t *hist;               // 256 * sort_blocks(n)
+    uint32_t *blocksum;           // compaction block sums
+    uint32_t *flags;              // n
+    uint32_t *surv_rows;          // n * DP canonical rows, sum order
+    uint32_t *surv_orig;          // n original row numbers, sum order
+    uint32_t *reps;               // kMaxReps * DP
+    uint32_t *sky_rows;           // (n + tile) * DP canonical rows, skyline order
+    uint32_t *cand;               // (n + tile) * DP canonical rows, partition order
+    uint32_t *tmin;               // tiles * DP per-tile minima
+    uint32_t *perm;               // n: partition position -> skyline position
+    int32_t *res;                 // n: result per partition position
+    uint32_t *steps;              // K widths
+    uint32_t *magic;              // K * 4 multiply-high constants (m, s1, s2, delta)
+    size_t bytes;
+};
+
+int64_t sort_blocks(int64_t n);
+int64_t scan_blocks(int64_t n);
+size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws);
+
+// Granlund & Montgomery (1994), unsigned division by a run-time invariant
+// divisor (their Fig. 4.1): with l = ceil(log2 delta),
+// m = floor(2^32 (2^l - delta) / delta) + 1, s1 = min(l, 1), s2 = max(l - 1, 0),
+// floor(v / delta) = (t + ((v - t) >> s1)) >> s2 where t = mulhi(m, v).
+void udiv_magic(uint32_t delta, uint32_t *m, uint32_t *s1, uint32_t *s2);
+
+__device__ __forceinline__ uint32_t udiv(uint32_t v, uint32_t m, uint32_t s1, uint32_t s2) {
+    uint32_t t = __umulhi(m, v);
+    return (t + ((v - t) >> s1)) >> s2;
+}
+
+// Canonical value: smaller is better after this map (GRES_MAX reads ~v).
+__device__ __forceinline__ uint32_t canon(uint32_t v, int dir) { return dir ? ~v : v; }
+
+// ---- kernel launchers (each queues on `st`, returns the launch error) -------
+cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
+cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, cudaStream_t st);
+cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
+                              int max_passes, cudaStream_t st);
+cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,
+                           Workspace &ws, int64_t *d_sky_idx, cudaStream_t st);
+cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir, int k,
+                              const gres_plan_cfg &cfg, Workspace &ws,
+                              const int64_t *d_sky_idx, int32_t *d_step_idx,
+                              unsigned long long *d_tests, cudaStream_t st);
+cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps, int k,
+                         uint32_t *d_out, cudaStream_t st);
+
+}  // namespace gres

@@ -1,0 +1,647 @@
+// gres_stage.cu -- grid resistance of every skyline tuple (Def. 2, Algorithm 1).
+//
+// Inputs: the canonical skyline rows (smaller is better) from skyline.cu. By
+// the stability of gres (Sec. 3.2) the candidate dominators are the skyline
+// itself.
+//
+// For a target t and a width delta, the projection of t is the cell with
+// lowest corner Lv = floor(t / delta) * delta (Sec. 2). On the original
+// values, floor(s/delta) <= floor(t/delta) iff s <= Uv = Lv + delta - 1, and
+// floor(s/delta) < floor(t/delta) iff s < Lv. So s's projection dominates
+// t's (Def. 1 on projections) iff s <= U in every attribute and s < L in one,
+// where (U, L) = (Uv, Lv) for smaller-is-better and, on canonical values
+// ~v, (U, L) = (~Lv, ~Uv) for larger-is-better. The kernel therefore never
+// projects candidates: one division per (t, step, attribute) gives the
+// bounds, and each (candidate, step) test is 2d unsigned compares.
+//
+// Pruning (speed only; results do not depend on it):
+//   * candidates are grouped into 32-row tiles after a Grid / Angular /
+//     Sliced partitioning (Sec. 3.1) so that tiles are spatially tight;
+//   * s can dominate t at width delta only if delta > max_i (s_i - t_i)^+
+//     (a worse attribute must share t's cell), so with the tile minimum
+//     tmin a tile is irrelevant for every step with delta <= e_tile =
+//     max_i (tmin_i - t_i)^+, and for every step if no tmin_i < t_i;
+//   * tiles are visited in ascending order of their first relevant step,
+//     and the scan of a target stops at the first step that has a
+//     dominator (the minimum over steps, Def. 2); steps are never bisected
+//     since membership is not monotone in the width.
+//
+// Mapping: one warp per target tuple (dynamic queue). Lane l holds the
+// bounds of steps w0 + 32 j + l (j < SLOTS) in registers; every candidate
+// row of a tile is broadcast to all lanes; a ballot per slot and __ffs give
+// the first dominated step. The candidate rows and tile minima are staged in
+// shared memory with cp.async when they fit (they do for skylines up to
+// about 6,900 rows at d = 6), otherwise read through L1.
+#include "gres_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace gres {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- steps: widths and Granlund-Montgomery constants, passed by value -------
+constexpr int kStepChunk = 2000;
+struct StepChunk {
+    int off;
+    int count;
+    uint4 e[kStepChunk];   // (m, s1, s2, delta)
+};
+
+__global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
+        const uint4 v = c.e[i];
+        steps[c.off + i] = v.w;
+        reinterpret_cast<uint4 *>(magic)[c.off + i] = v;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void ld_row(const uint32_t *base, long long r, uint32_t (&x)[D]) {
+    constexpr int DP = padded_dims(D);
+    const uint4 *p = reinterpret_cast<const uint4 *>(base + r * DP);
+    uint4 a = p[0];
+    x[0] = a.x;
+    if (D > 1) x[1 < D ? 1 : 0] = a.y;
+    if (D > 2) x[2 < D ? 2 : 0] = a.z;
+    if (D > 3) x[3 < D ? 3 : 0] = a.w;
+    if (DP == 8) {
+        uint4 b = p[1];
+        if (D > 4) x[4 < D ? 4 : 0] = b.x;
+        if (D > 5) x[5 < D ? 5 : 0] = b.y;
+        if (D > 6) x[6 < D ? 6 : 0] = b.z;
+        if (D > 7) x[7 < D ? 7 : 0] = b.w;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void ldg_row(const uint32_t *base, long long r, uint32_t (&x)[D]) {
+    constexpr int DP = padded_dims(D);
+    const uint4 *p = reinterpret_cast<const uint4 *>(base + r * DP);
+    uint4 a = __ldg(p);
+    x[0] = a.x;
+    if (D > 1) x[1 < D ? 1 : 0] = a.y;
+    if (D > 2) x[2 < D ? 2 : 0] = a.z;
+    if (D > 3) x[3 < D ? 3 : 0] = a.w;
+    if (DP == 8) {
+        uint4 b = __ldg(p + 1);
+        if (D > 4) x[4 < D ? 4 : 0] = b.x;
+        if (D > 5) x[5 < D ? 5 : 0] = b.y;
+        if (D > 6) x[6 < D ? 6 : 0] = b.z;
+        if (D > 7) x[7 < D ? 7 : 0] = b.w;
+    }
+}
+
+// Per-attribute range of the skyline (for the partition coordinates) and a
+// reset of the sort-key range for the partition sort.
+template <int D>
+__global__ void k_sky_range(const uint32_t *sky_rows, WsHeader *h) {
+    const long long S = h->n_sky;
+    uint32_t lo[D], hi[D];
+    #pragma unroll
+    for (int i = 0; i < D; i++) { lo[i] = 0xFFFFFFFFu; hi[i] = 0u; }
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < S;
+         j += (long long)gridDim.x * blockDim.x) {
+        uint32_t x[D];
+        ld_row<D>(sky_rows, j, x);
+        #pragma unroll
+        for (int i = 0; i < D; i++) { lo[i] = min(lo[i], x[i]); hi[i] = max(hi[i], x[i]); }
+    }
+    #pragma unroll
+    for (int i = 0; i < D; i++) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[i] = min(lo[i], __shfl_xor_sync(kFull, lo[i], o));
+            hi[i] = max(hi[i], __shfl_xor_sync(kFull, hi[i], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&h->lo[i], lo[i]);
+            atomicMax(&h->hi[i], hi[i]);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h->key_min = ~0ull;
+        h->key_max = 0ull;
+    }
+}
+
+__global__ void k_reset_keyrange(WsHeader *h) {
+    h->key_min = ~0ull;
+    h->key_max = 0ull;
+}
+
+struct PartArgs {
+    int scheme;      // gres_part
+    int m;           // GRID / ANGULAR slices
+    int p;           // SLICED partitions
+    int dim;         // SLICED attribute
+    int sec;         // attribute of the order inside a partition
+    unsigned long long thr[64];   // ANGULAR: tan^2(j pi / 2m) * 2^32, j = 1 .. m-1
+};
+
+// Warp-reduced atomic min/max of the sort-key range; lanes without an item
+// pass valid = false.
+__device__ __forceinline__ void key_minmax(unsigned long long k, bool valid, WsHeader *h) {
+    unsigned long long kmin = valid ? k : ~0ull, kmax = valid ? k : 0ull;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long a = __shfl_xor_sync(kFull, kmin, o);
+        unsigned long long b = __shfl_xor_sync(kFull, kmax, o);
+        kmin = a < kmin ? a : kmin;
+        kmax = b > kmax ? b : kmax;
+    }
+    if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
+        atomicMin(&h->key_min, kmin);
+        atomicMax(&h->key_max, kmax);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&x)[D], int q) {
+    uint32_t v = 0;
+    #pragma unroll
+    for (int i = 0; i < D; i++) v = i == q ? x[i] : v;
+    return v;
+}
+
+// Partition numbers (Sec. 3.1) on coordinates x = v - lo (canonical):
+//   GRID:    c_i = floor(x_i m / (hi_i - lo_i + 1)), p = sum_i c_i m^i
+//   ANGULAR: phi_i = atan2(sqrt(sum_{j>i} x_j^2), x_i); bin_i = number of
+//            thresholds j pi / 2m reached, decided exactly as
+//            (Y << 32) >= X * thr_j in 128-bit integers (Eq. 1)
+//   SLICED:  first pass keys on x_dim; the slice comes from the rank.
+// Sort key = partition << 32 | x_sec (order inside a partition), value = row.
+template <int D>
+__global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
+                            unsigned long long *keys, uint32_t *vals) {
+    const long long S = h->n_sky;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long start = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // every lane of a warp takes part in key_minmax: loop to a warp-uniform bound
+    const long long lim = ((S + 31) / 32) * 32;
+    for (long long j = start; j < lim; j += stride) {
+        unsigned long long key = 0;
+        const bool valid = j < S;
+        if (valid) {
+            uint32_t x[D];
+            ld_row<D>(sky_rows, j, x);
+            #pragma unroll
+            for (int i = 0; i < D; i++) x[i] -= h->lo[i];
+            unsigned long long pid = 0;
+            if (a.scheme == GRES_PART_GRID) {
+                unsigned long long w = 1;
+                #pragma unroll
+                for (int i = 0; i < D; i++) {
+                    const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
+                    pid += ((unsigned long long)x[i] * (unsigned long long)a.m) / span * w;
+                    w *= (unsigned long long)a.m;
+                }
+                key = (pid << 32) | pick<D>(x, a.sec);
+            } else if (a.scheme == GRES_PART_ANGULAR) {
+                unsigned long long w = 1;
+                #pragma unroll
+                for (int i = 0; i + 1 < D; i++) {
+                    const unsigned __int128 X = (unsigned __int128)x[i] * x[i];
+                    unsigned __int128 Y = 0;
+                    #pragma unroll
+                    for (int q = i + 1; q < D; q++) Y += (unsigned __int128)x[q] * x[q];
+                    int bin = 0;
+                    if (!(X == 0 && Y == 0)) {
+                        for (int t = 1; t < a.m; t++)
+                            if ((Y << 32) >= X * (unsigned __int128)a.thr[t]) bin = t;
+                    }
+                    pid += (unsigned long long)bin * w;
+                    w *= (unsigned long long)a.m;
+                }
+                key = (pid << 32) | pick<D>(x, a.sec);
+            } else {  // SLICED, first pass
+                key = pick<D>(x, a.dim);
+            }
+        }
+        if (valid) {
+            keys[j] = key;
+            vals[j] = (uint32_t)j;
+        }
+        key_minmax(key, valid, h);
+    }
+}
+
+// SLICED second pass (after k_reset_keyrange): the row of rank r in the
+// order of x_dim falls in slice floor(r p / S) (Sec. 3.1); the new key orders
+// rows by (slice, x_sec). Reads the sorted buffer, writes buffer 0 at the same
+// index (in place when the sorted buffer is buffer 0).
+template <int D>
+__global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
+                              unsigned long long *keys0, uint32_t *vals0, const uint32_t *vals1) {
+    const long long S = h->n_sky;
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long lim = ((S + 31) / 32) * 32;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < lim; r += stride) {
+        unsigned long long key = 0;
+        uint32_t j = 0;
+        const bool valid = r < S;
+        if (valid) {
+            j = vals[r];
+            uint32_t x[D];
+            ld_row<D>(sky_rows, j, x);
+            const unsigned long long slice =
+                (unsigned long long)r * (unsigned long long)a.p / (unsigned long long)S;
+            key = (slice << 32) | (unsigned long long)(pick<D>(x, a.sec) - h->lo[a.sec]);
+        }
+        if (valid) {
+            keys0[r] = key;
+            vals0[r] = j;
+        }
+        key_minmax(key, valid, h);
+    }
+}
+
+// Candidate rows in partition order, padded to whole 32-row tiles with
+// sentinel rows (all ones: never dominate), and each tile's per-attribute
+// minimum. One warp per tile.
+template <int D>
+__global__ void k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1,
+                          const WsHeader *h, int identity, uint32_t *cand, uint32_t *tmin,
+                          uint32_t *perm) {
+    constexpr int DP = padded_dims(D);
+    const long long S = h->n_sky;
+    const long long T = (S + kTileRows - 1) / kTileRows;
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    const int lane = threadIdx.x & 31;
+    const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < T; tile += wstride) {
+        const long long i = tile * kTileRows + lane;
+        uint32_t x[DP];
+        if (i < S) {
+            const uint32_t j = identity ? (uint32_t)i : vals[i];
+            perm[i] = j;
+            const uint4 *p = reinterpret_cast<const uint4 *>(sky_rows + (long long)j * DP);
+            uint4 a = p[0];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            if (DP == 8) { uint4 b = p[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
+        } else {
+            #pragma unroll
+            for (int q = 0; q < DP; q++) x[q] = kSentinel;
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(cand + i * DP);
+        dst[0] = make_uint4(x[0], x[1], x[2], x[3]);
+        if (DP == 8) dst[1] = make_uint4(x[4 % DP], x[5 % DP], x[6 % DP], x[7 % DP]);
+        uint32_t mn[DP];
+        #pragma unroll
+        for (int q = 0; q < DP; q++) {
+            uint32_t v = x[q];
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+            mn[q] = v;
+        }
+        if (lane == 0) {
+            uint4 *td = reinterpret_cast<uint4 *>(tmin + tile * DP);
+            td[0] = make_uint4(mn[0], mn[1], mn[2], mn[3]);
+            if (DP == 8) td[1] = make_uint4(mn[4 % DP], mn[5 % DP], mn[6 % DP], mn[7 % DP]);
+        }
+    }
+}
+
+// ---- the pairwise grid-dominance kernel ------------------------------------
+struct DomArgs {
+    const uint32_t *cand;     // T*32 rows, DP words each (partition order)
+    const uint32_t *tmin;     // T rows, DP words each
+    const uint32_t *magic;    // K * 4: (m, s1, s2, delta)
+    WsHeader *hdr;
+    int32_t *res;             // per partition position
+    unsigned long long *tests;
+    int K;
+    int dir;
+    int smem_words;           // dynamic shared memory, in words
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+template <int D>
+__host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 ? 384 : 256); }
+
+constexpr int kTileKeys = 8;                 // tile keys per lane in one selection round
+constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
+template <int D, int SLOTS, bool RES>
+__device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *cand, const uint32_t *tmin,
+                                              uint32_t *wsteps, long long S, long long T) {
+    constexpr int WS = 32 * SLOTS;
+    const int lane = threadIdx.x & 31;
+    const int K = a.K;
+    unsigned long long my_tests = 0;
+    for (;;) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(&a.hdr->work_next, 1u);
+        i = __shfl_sync(kFull, i, 0);
+        if ((long long)i >= S) break;
+        uint32_t t[D];
+        if (RES) ld_row<D>(cand, i, t); else ldg_row<D>(cand, i, t);
+        int result = K;
+        for (int w0 = 0; w0 < K; w0 += WS) {
+            const int wcount = min(WS, K - w0);
+            uint32_t U[SLOTS][D], L[SLOTS][D];
+            #pragma unroll
+            for (int j = 0; j < SLOTS; j++) {
+                const int k = w0 + 32 * j + lane;
+                if (k < K) {
+                    const uint4 mg = __ldg(reinterpret_cast<const uint4 *>(a.magic) + k);
+                    const uint32_t delta = mg.w;
+                    wsteps[32 * j + lane] = delta;
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) {
+                        const uint32_t v = a.dir ? ~t[q] : t[q];
+                        const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
+                        const uint32_t uv = lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+                        U[j][q] = a.dir ? ~lv : uv;
+                        L[j][q] = a.dir ? ~uv : lv;
+                    }
+                } else {
+                    wsteps[32 * j + lane] = 0xFFFFFFFFu;
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) { U[j][q] = 0u; L[j][q] = 0u; }
+                }
+            }
+            __syncwarp();
+            int best = wcount;
+            for (long long tc = 0; tc < T && best > 0; tc += 32 * kTileKeys) {
+                uint32_t key[kTileKeys];
+                #pragma unroll
+                for (int e = 0; e < kTileKeys; e++) {
+                    key[e] = kNoTile;
+                    const long long tile = tc + 32 * e + lane;
+                    if (tile < T) {
+                        uint32_t mn[D];
+                        if (RES) ld_row<D>(tmin, tile, mn); else ldg_row<D>(tmin, tile, mn);
+                        uint32_t emax = 0;
+                        bool can = false;
+                        #pragma unroll
+                        for (int q = 0; q < D; q++) {
+                            emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
+                            can |= mn[q] < t[q];
+                        }
+                        if (can) {
+                            int lo = 0, hi = wcount;   // first window step with delta > emax
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (wsteps[mid] <= emax) lo = mid + 1; else hi = mid;
+                            }
+                            if (lo < best) key[e] = ((uint32_t)lo << 16) | (uint32_t)(32 * e + lane);
+                        }
+                    }
+                }
+                for (;;) {
+                    uint32_t lm = key[0];
+                    #pragma unroll
+                    for (int e = 1; e < kTileKeys; e++) lm = min(lm, key[e]);
+                    const uint32_t mkey = __reduce_min_sync(kFull, lm);
+                    if (mkey == kNoTile) break;
+                    const int klo = (int)(mkey >> 16);
+                    if (klo >= best) break;
+                    #pragma unroll
+                    for (int e = 0; e < kTileKeys; e++) key[e] = key[e] == mkey ? kNoTile : key[e];
+                    const long long tile = tc + (mkey & 0xFFFFu);
+                    const int jlo = klo >> 5, jhi = (best - 1) >> 5;
+                    const long long r0 = tile * kTileRows;
+                    #pragma unroll
+                    for (int j = 0; j < SLOTS; j++) {
+                        if (j < jlo || j > jhi) continue;
+                        bool hit = false;
+                        #pragma unroll 8
+                        for (int r = 0; r < kTileRows; r++) {
+                            uint32_t s[D];
+                            if (RES) ld_row<D>(cand, r0 + r, s); else ldg_row<D>(cand, r0 + r, s);
+                            bool le = true, lt = false;
+                            #pragma unroll
+                            for (int q = 0; q < D; q++) {
+                                le &= s[q] <= U[j][q];
+                                lt |= s[q] < L[j][q];
+                            }
+                            hit |= le & lt;
+                        }
+                        my_tests += kTileRows * 32;
+                        const unsigned msk = __ballot_sync(kFull, hit);
+                        if (msk) {
+                            best = min(best, 32 * j + __ffs(msk) - 1);
+                            break;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (best < wcount) { result = w0 + best; break; }
+        }
+        if (lane == 0) a.res[i] = result;
+    }
+    if (a.tests && lane == 0 && my_tests) atomicAdd(a.tests, my_tests);
+}
+
+template <int D, int SLOTS>
+__global__ void __launch_bounds__(dom_threads<D>(), 1)
+k_dominance(DomArgs a) {
+    constexpr int DP = padded_dims(D);
+    constexpr int WS = 32 * SLOTS;
+    extern __shared__ __align__(16) uint32_t sm[];
+    const long long S = a.hdr->n_sky;
+    if (S == 0) return;
+    const long long T = (S + kTileRows - 1) / kTileRows;
+    const int nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    uint32_t *wsteps = sm + warp * WS;
+    uint32_t *res_base = sm + nwarps * WS;
+    const long long cand_words = T * kTileRows * DP;
+    const long long need = cand_words + T * DP;
+    const bool resident = need <= (long long)a.smem_words - (long long)nwarps * WS;
+    if (resident) {
+        const long long n16a = cand_words / 4, n16b = (T * DP) / 4;
+        for (long long v = threadIdx.x; v < n16a; v += blockDim.x) cp_async16(res_base + 4 * v, a.cand + 4 * v);
+        for (long long v = threadIdx.x; v < n16b; v += blockDim.x)
+            cp_async16(res_base + cand_words + 4 * v, a.tmin + 4 * v);
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        dom_warp_loop<D, SLOTS, true>(a, res_base, res_base + cand_words, wsteps, S, T);
+    } else {
+        dom_warp_loop<D, SLOTS, false>(a, a.cand, a.tmin, wsteps, S, T);
+    }
+}
+
+__global__ void k_scatter_res(const int32_t *res, const uint32_t *perm, const WsHeader *h, int32_t *out) {
+    const long long S = h->n_sky;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S;
+         i += (long long)gridDim.x * blockDim.x)
+        out[perm[i]] = res[i];
+}
+
+__global__ void k_gproj(const uint32_t *v, long long count, StepChunk c, uint32_t *out) {
+    const long long total = count * c.count;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const long long j = x / count, i = x - j * count;
+        const uint4 mg = c.e[j];
+        out[(c.off + j) * count + i] = udiv(v[i], mg.x, mg.y, mg.z);
+    }
+}
+
+int g_sm_count = 0;
+int g_smem_optin = 0;
+
+cudaError_t device_props() {
+    if (g_sm_count) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    return cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+}
+
+template <int D, int SLOTS>
+cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
+    static bool configured = false;
+    const int smem = g_smem_optin;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_dominance<D, SLOTS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    a.smem_words = smem / 4;
+    k_dominance<D, SLOTS><<<g_sm_count, dom_threads<D>(), smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D, int SLOTS>
+cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Workspace &ws,
+                          int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
+    const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count * 4);
+    k_sky_range<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr);
+    const int scheme = cfg.scheme;
+    PartArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.scheme = scheme;
+    pa.m = cfg.m;
+    pa.p = cfg.p;
+    pa.dim = cfg.slice_dim;
+    pa.sec = D > 1 ? (scheme == GRES_PART_SLICED ? (cfg.slice_dim + 1) % D : 0) : 0;
+    if (scheme == GRES_PART_ANGULAR) {
+        const double pi = 3.14159265358979323846;
+        for (int j = 1; j < cfg.m && j < 64; j++) {
+            const double t = std::tan((double)j * pi / (2.0 * (double)cfg.m));
+            pa.thr[j] = (unsigned long long)std::llround(t * t * 4294967296.0);
+        }
+    }
+    cudaError_t e;
+    if (scheme != GRES_PART_NONE) {
+        k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]);
+        e = launch_radix_sort(ws, n, &ws.hdr->n_sky, 8, st);
+        if (e != cudaSuccess) return e;
+        if (scheme == GRES_PART_SLICED) {
+            k_reset_keyrange<<<1, 1, 0, st>>>(ws.hdr);
+            k_sliced_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0], ws.vals[1]);
+            e = launch_radix_sort(ws, n, &ws.hdr->n_sky, 8, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    const int pb = (int)std::min<int64_t>((n + 255) / 256 + 1, (int64_t)g_sm_count * 8);
+    k_permute<D><<<pb, 256, 0, st>>>(ws.sky_rows, ws.vals[0], ws.vals[1], ws.hdr,
+                                     scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.perm);
+    DomArgs a;
+    a.cand = ws.cand;
+    a.tmin = ws.tmin;
+    a.magic = ws.magic;
+    a.hdr = ws.hdr;
+    a.res = ws.res;
+    a.tests = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;
+    a.K = k;
+    a.dir = dir;
+    a.smem_words = 0;
+    e = launch_dom<D, SLOTS>(a, st);
+    if (e != cudaSuccess) return e;
+    k_scatter_res<<<pb, 256, 0, st>>>(ws.res, ws.perm, ws.hdr, d_step_idx);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t gres_stage_d(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Workspace &ws,
+                         int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
+    if (cfg.slots == 4) return gres_stage_ds<D, 4>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+    return gres_stage_ds<D, 8>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+}
+
+}  // namespace
+
+cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, cudaStream_t st) {
+    StepChunk c;
+    for (int off = 0; off < k; off += kStepChunk) {
+        c.off = off;
+        c.count = std::min(kStepChunk, k - off);
+        for (int i = 0; i < c.count; i++) {
+            uint32_t m, s1, s2;
+            udiv_magic(h_steps[off + i], &m, &s1, &s2);
+            c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
+        }
+        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int dir, int k,
+                              const gres_plan_cfg &cfg, Workspace &ws,
+                              const int64_t * /*d_sky_idx*/, int32_t *d_step_idx,
+                              unsigned long long *d_tests, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+    switch (d) {
+        case 1: return gres_stage_d<1>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 2: return gres_stage_d<2>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 3: return gres_stage_d<3>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 4: return gres_stage_d<4>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 5: return gres_stage_d<5>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 6: return gres_stage_d<6>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 7: return gres_stage_d<7>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        case 8: return gres_stage_d<8>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps, int k,
+                         uint32_t *d_out, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+    StepChunk c;
+    for (int off = 0; off < k; off += kStepChunk) {
+        c.off = off;
+        c.count = std::min(kStepChunk, k - off);
+        for (int i = 0; i < c.count; i++) {
+            uint32_t m, s1, s2;
+            udiv_magic(h_steps[off + i], &m, &s1, &s2);
+            c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
+        }
+        const long long total = (long long)count * c.count;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g_sm_count * 8);
+        k_gproj<<<blocks, 256, 0, st>>>(d_values, (long long)count, c, d_out);
+    }
+    return cudaGetLastError();
+}
+
+void udiv_magic(uint32_t delta, uint32_t *m, uint32_t *s1, uint32_t *s2) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)delta) l++;   // l = ceil(log2 delta)
+    const unsigned long long two32 = 1ull << 32;
+    const unsigned long long num = two32 * ((1ull << l) - (unsigned long long)delta);
+    *m = (uint32_t)(num / delta + 1ull);
+    *s1 = l < 1 ? (uint32_t)l : 1u;
+    *s2 = l > 1 ? (uint32_t)(l - 1) : 0u;
+}
+
+}  // namespace gres

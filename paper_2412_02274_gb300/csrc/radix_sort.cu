@@ -1,0 +1,172 @@
+// radix_sort.cu -- stable LSD radix sort of (uint64 key, uint32 value) pairs.
+//
+// Sorts ws.keys[0]/ws.vals[0] by key. The element count and the key range
+// (hdr->key_min, hdr->key_max) live on the device, so the number of 8-bit
+// digit passes that do any work, E = ceil(bits(key_max - key_min) / 8), is
+// decided on the device: passes p >= E return at once. Pass p reads buffer
+// p & 1 and writes buffer (p + 1) & 1, so the result is in buffer E & 1,
+// which a last one-thread kernel records in hdr->sorted_sel. Digits are
+// taken from key - key_min.
+//
+// Each pass is three kernels: per-block digit histograms, one exclusive scan
+// over the (digit-major, block-minor) histogram table, and a stable scatter
+// in which each block ranks its items per digit in input order (warp
+// match_any for ranks within a warp, a per-digit prefix over warps for the
+// block, a running per-digit carry across the block's rounds).
+#include "gres_internal.cuh"
+
+namespace gres {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;   // 4096 items per block
+constexpr int kWarps = kThreads / 32;
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kThreads)
+k_hist(WsHeader *h, const unsigned long long *keys_in, uint32_t *hist, const long long *d_n, int pass) {
+    if (pass >= radix_passes(h)) return;
+    const long long n = *d_n;
+    const long long G = (n + kTile - 1) / kTile;
+    if ((long long)blockIdx.x >= G) return;
+    __shared__ uint32_t sh[256];
+    sh[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long kmin = h->key_min;
+    const int shift = 8 * pass;
+    const long long b0 = (long long)blockIdx.x * kTile;
+    const long long b1 = min(b0 + kTile, n);
+    for (long long i = b0 + threadIdx.x; i < b1; i += kThreads) {
+        uint32_t dg = (uint32_t)(((keys_in[i] - kmin) >> shift) & 255ull);
+        atomicAdd(&sh[dg], 1u);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * G + blockIdx.x] = sh[threadIdx.x];
+}
+
+// Exclusive scan of hist[0 .. 256*G) in place (one block).
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(WsHeader *h, uint32_t *hist, const long long *d_n, int pass) {
+    if (pass >= radix_passes(h)) return;
+    const long long n = *d_n;
+    const long long G = (n + kTile - 1) / kTile;
+    const long long total = 256 * G;
+    if (total == 0) return;
+    const long long chunk = (total + kScanThreads - 1) / kScanThreads;
+    const long long c0 = (long long)threadIdx.x * chunk;
+    const long long c1 = min(c0 + chunk, total);
+    uint32_t local = 0;
+    for (long long i = c0; i < c1; i++) local += hist[i];
+    // block exclusive scan of `local`
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        uint32_t vi = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = vi - v;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[w] + incl - local;
+    for (long long i = c0; i < c1; i++) {
+        uint32_t c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_in,
+          unsigned long long *keys_out, uint32_t *vals_out, const uint32_t *hist,
+          const long long *d_n, int pass) {
+    if (pass >= radix_passes(h)) return;
+    const long long n = *d_n;
+    const long long G = (n + kTile - 1) / kTile;
+    if ((long long)blockIdx.x >= G) return;
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wcnt[kWarps][256];
+    __shared__ uint32_t woff[kWarps][256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    base[tid] = hist[(long long)tid * G + blockIdx.x];
+    for (int j = 0; j < kWarps; j++) wcnt[j][tid] = 0;
+    __syncthreads();
+    const unsigned long long kmin = h->key_min;
+    const int shift = 8 * pass;
+    const long long b0 = (long long)blockIdx.x * kTile;
+    const long long b1 = min(b0 + kTile, n);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int r = 0; r < kItems; r++) {
+        const long long i = b0 + (long long)r * kThreads + tid;
+        const bool valid = i < b1;
+        unsigned long long key = 0;
+        uint32_t val = 0;
+        uint32_t dg = 256;  // invalid items share a digit no real item has
+        if (valid) {
+            key = keys_in[i];
+            val = vals_in[i];
+            dg = (uint32_t)(((key - kmin) >> shift) & 255ull);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && rank == 0) wcnt[w][dg] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = base[tid];
+            #pragma unroll
+            for (int j = 0; j < kWarps; j++) {
+                uint32_t c = wcnt[j][tid];
+                wcnt[j][tid] = 0;
+                woff[j][tid] = run;
+                run += c;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = woff[w][dg] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_sort_done(WsHeader *h) { h->sorted_sel = (unsigned)(radix_passes(h) & 1); }
+
+}  // namespace
+
+int64_t sort_blocks(int64_t n) { return (n + kTile - 1) / kTile; }
+
+// Queues up to `max_passes` digit passes on ws.keys[0]/ws.vals[0] (count in
+// *d_n, at most n_max). The sorted data ends in buffer hdr->sorted_sel.
+cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
+                              int max_passes, cudaStream_t st) {
+    const int64_t G = sort_blocks(n_max);
+    if (G == 0) {
+        k_sort_done<<<1, 1, 0, st>>>(ws.hdr);
+        return cudaGetLastError();
+    }
+    for (int p = 0; p < max_passes; p++) {
+        const int in = p & 1, out = (p + 1) & 1;
+        k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p);
+        k_scan<<<1, kScanThreads, 0, st>>>(ws.hdr, ws.hist, d_n, p);
+        k_scatter<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.vals[in], ws.keys[out],
+                                                    ws.vals[out], ws.hist, d_n, p);
+    }
+    k_sort_done<<<1, 1, 0, st>>>(ws.hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace gres

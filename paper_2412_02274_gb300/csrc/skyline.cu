@@ -1,0 +1,418 @@
+// skyline.cu -- Sky(r) (Def. 1) by a sort-by-sum pass with block dominance filters.
+//
+// Pipeline (all sizes after n live in the workspace header):
+//   1. keys:   canonical rows (smaller is better; GRES_MAX reads ~v) and the
+//              key f(t) = sum of the canonical values. f is monotone, so
+//              s dominates t implies f(s) < f(t): in ascending key order a
+//              tuple can only be dominated by an earlier one (the ordering
+//              of sort-filter-skyline, cited in Sec. 4).
+//   2. sort:   stable radix sort of (key, row) -- ties keep row order.
+//   3. reps:   the first R rows of the order; those dominated by another of
+//              them are dropped (Representative Filtering, Sec. 3.1). The
+//              rest are skyline tuples: only earlier, smaller-key rows could
+//              dominate them and those are all representatives.
+//   4. filter: every row is tested against the representatives.
+//   5. compact the survivors, in key order.
+//   6. final:  each survivor is tested against every EARLIER survivor; it is
+//              in the skyline iff none dominates it. (If t is dominated, a
+//              skyline tuple with a smaller key dominates it, and skyline
+//              tuples always survive step 4.)
+//   7. flags by original row -> ascending row numbers, plus the canonical
+//      skyline rows for the gres stage.
+#include "gres_internal.cuh"
+
+#include <algorithm>
+
+namespace gres {
+
+namespace {
+
+constexpr int kCT = 256;            // threads per compaction / filter block
+constexpr int kPer = 4;             // items per thread
+constexpr int kCB = kCT * kPer;     // items per compaction block
+constexpr int kTriThreads = 256;
+constexpr int kTriChunk = 1024;     // candidate rows staged per round
+
+template <int D>
+__device__ __forceinline__ void load_canon(const uint32_t *data, long long row, int dir, uint32_t (&x)[D]) {
+    const uint32_t *p = data + row * D;
+    #pragma unroll
+    for (int i = 0; i < D; i++) x[i] = canon(p[i], dir);
+}
+
+template <int D>
+__device__ __forceinline__ void load_row(const uint32_t *base, long long r, uint32_t (&x)[D]) {
+    constexpr int DP = padded_dims(D);
+    const uint4 *p = reinterpret_cast<const uint4 *>(base + r * DP);
+    uint4 a = p[0];
+    x[0] = a.x;
+    if (D > 1) x[1 < D ? 1 : 0] = a.y;
+    if (D > 2) x[2 < D ? 2 : 0] = a.z;
+    if (D > 3) x[3 < D ? 3 : 0] = a.w;
+    if (DP == 8) {
+        uint4 b = p[1];
+        if (D > 4) x[4 < D ? 4 : 0] = b.x;
+        if (D > 5) x[5 < D ? 5 : 0] = b.y;
+        if (D > 6) x[6 < D ? 6 : 0] = b.z;
+        if (D > 7) x[7 < D ? 7 : 0] = b.w;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void store_row(uint32_t *base, long long r, const uint32_t (&x)[D]) {
+    constexpr int DP = padded_dims(D);
+    uint32_t y[DP];
+    #pragma unroll
+    for (int i = 0; i < DP; i++) y[i] = i < D ? x[i < D ? i : 0] : 0u;
+    uint4 *p = reinterpret_cast<uint4 *>(base + r * DP);
+    p[0] = make_uint4(y[0], y[1], y[2], y[3]);
+    if (DP == 8) p[1] = make_uint4(y[4 % DP], y[5 % DP], y[6 % DP], y[7 % DP]);
+}
+
+// Def. 1 on canonical rows: s dominates t.
+template <int D>
+__device__ __forceinline__ bool dominates(const uint32_t (&s)[D], const uint32_t (&t)[D]) {
+    bool le = true, lt = false;
+    #pragma unroll
+    for (int i = 0; i < D; i++) {
+        le &= s[i] <= t[i];
+        lt |= s[i] < t[i];
+    }
+    return le && lt;
+}
+
+// Exclusive scan over a kCT-thread block; *total gets the block sum.
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t wsum[kCT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    #pragma unroll
+    for (int j = 0; j < kCT / 32; j++) {
+        uint32_t x = wsum[j];
+        before += j < w ? x : 0u;
+        all += x;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
+
+__global__ void k_init(WsHeader *h, long long n) {
+    if (threadIdx.x == 0) {
+        h->key_min = ~0ull;
+        h->key_max = 0ull;
+        h->n_rows = n;
+        h->n_surv = 0;
+        h->n_sky = 0;
+        h->n_reps = 0;
+        h->work_next = 0;
+        h->status = 0;
+        h->sorted_sel = 0;
+    }
+    if (threadIdx.x < kMaxD) {
+        h->lo[threadIdx.x] = 0xFFFFFFFFu;
+        h->hi[threadIdx.x] = 0u;
+    }
+}
+
+template <int D>
+__global__ void k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys,
+                       uint32_t *vals, WsHeader *h) {
+    unsigned long long kmin = ~0ull, kmax = 0ull;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        uint32_t x[D];
+        load_canon<D>(data, i, dir, x);
+        unsigned long long k = 0;
+        #pragma unroll
+        for (int j = 0; j < D; j++) k += x[j];
+        keys[i] = k;
+        vals[i] = (uint32_t)i;
+        kmin = k < kmin ? k : kmin;
+        kmax = k > kmax ? k : kmax;
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, o);
+        unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, o);
+        kmin = a < kmin ? a : kmin;
+        kmax = b > kmax ? b : kmax;
+    }
+    if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
+        atomicMin(&h->key_min, kmin);
+        atomicMax(&h->key_max, kmax);
+    }
+}
+
+// Representatives: the first R rows in key order, minus those dominated by
+// another of them. One block of kMaxReps threads.
+template <int D>
+__global__ void __launch_bounds__(kMaxReps)
+k_reps(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
+       int R, uint32_t *reps, WsHeader *h) {
+    __shared__ uint32_t rows[kMaxReps * D];
+    __shared__ uint32_t wsum[kMaxReps / 32];
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    const int r_eff = (int)min((long long)R, n);
+    const int i = threadIdx.x;
+    uint32_t x[D];
+    if (i < r_eff) {
+        load_canon<D>(data, vals[i], dir, x);
+        #pragma unroll
+        for (int j = 0; j < D; j++) rows[i * D + j] = x[j];
+    }
+    __syncthreads();
+    bool keep = false;
+    if (i < r_eff) {
+        keep = true;
+        for (int j = 0; j < r_eff && keep; j++) {
+            uint32_t s[D];
+            #pragma unroll
+            for (int q = 0; q < D; q++) s[q] = rows[j * D + q];
+            if (dominates<D>(s, x)) keep = false;
+        }
+    }
+    // block compaction of the kept representatives
+    const int lane = i & 31, w = i >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int j = 0; j < kMaxReps / 32; j++) {
+        before += j < w ? wsum[j] : 0u;
+        all += wsum[j];
+    }
+    if (keep) {
+        const uint32_t pos = before + __popc(bal & ((1u << lane) - 1u));
+        store_row<D>(reps, pos, x);
+    }
+    if (i == 0) h->n_reps = all;
+}
+
+// Survivor flags (not dominated by any representative) in key order, plus
+// per-block counts for the compaction.
+template <int D>
+__global__ void __launch_bounds__(kCT)
+k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
+         const uint32_t *reps, const WsHeader *h, uint32_t *flags, uint32_t *blocksum) {
+    __shared__ uint32_t rs[kMaxReps * D];
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    const int nr = (int)h->n_reps;
+    for (int j = threadIdx.x; j < nr; j += kCT) {
+        uint32_t x[D];
+        load_row<D>(reps, j, x);
+        #pragma unroll
+        for (int q = 0; q < D; q++) rs[j * D + q] = x[q];
+    }
+    __syncthreads();
+    uint32_t cnt = 0;
+    const long long b0 = (long long)blockIdx.x * kCB;
+    #pragma unroll 1
+    for (int r = 0; r < kPer; r++) {
+        const long long p = b0 + r * kCT + threadIdx.x;
+        if (p >= n) break;
+        uint32_t x[D];
+        load_canon<D>(data, vals[p], dir, x);
+        bool alive = true;
+        for (int j = 0; j < nr; j++) {
+            uint32_t s[D];
+            #pragma unroll
+            for (int q = 0; q < D; q++) s[q] = rs[j * D + q];
+            if (dominates<D>(s, x)) { alive = false; break; }
+        }
+        flags[p] = alive ? 1u : 0u;
+        cnt += alive ? 1u : 0u;
+    }
+    uint32_t tot;
+    block_scan(cnt, &tot);
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of blocksum[0 .. nb) in place (one block); *total = sum.
+__global__ void __launch_bounds__(1024)
+k_scan_blocks(uint32_t *blocksum, long long nb, long long *total) {
+    __shared__ uint32_t wsum[32];
+    const long long chunk = (nb + 1023) / 1024;
+    const long long c0 = (long long)threadIdx.x * chunk;
+    const long long c1 = min(c0 + chunk, nb);
+    uint32_t local = 0;
+    for (long long i = c0; i < c1; i++) local += blocksum[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int j = 0; j < 32; j++) {
+        before += j < w ? wsum[j] : 0u;
+        all += wsum[j];
+    }
+    uint32_t run = before + incl - local;
+    for (long long i = c0; i < c1; i++) {
+        uint32_t c = blocksum[i];
+        blocksum[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) *total = all;
+}
+
+// Survivors, in key order: canonical rows and original row numbers.
+template <int D>
+__global__ void __launch_bounds__(kCT)
+k_compact_surv(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1,
+               long long n, const uint32_t *flags, const uint32_t *blocksum, uint32_t *surv_rows,
+               uint32_t *surv_orig, const WsHeader *h) {
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    uint32_t run = blocksum[blockIdx.x];
+    const long long b0 = (long long)blockIdx.x * kCB;
+    #pragma unroll 1
+    for (int r = 0; r < kPer; r++) {
+        const long long p = b0 + r * kCT + threadIdx.x;
+        const uint32_t f = p < n ? flags[p] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_scan(f, &tot);
+        if (f) {
+            const uint32_t row = vals[p];
+            uint32_t x[D];
+            load_canon<D>(data, row, dir, x);
+            store_row<D>(surv_rows, run + ex, x);
+            surv_orig[run + ex] = row;
+        }
+        run += tot;
+    }
+}
+
+// Final filter over survivors in key order: survivor q is a skyline tuple iff
+// no survivor j < q dominates it. Sets skyflag[original row].
+template <int D>
+__global__ void __launch_bounds__(kTriThreads)
+k_tri(const uint32_t *surv_rows, const uint32_t *surv_orig, const WsHeader *h, uint32_t *skyflag) {
+    constexpr int DP = padded_dims(D);
+    __shared__ __align__(16) uint32_t chunk[kTriChunk * DP];
+    const long long M = h->n_surv;
+    const long long q0 = (long long)blockIdx.x * kTriThreads;
+    if (q0 >= M) return;
+    const long long q = q0 + threadIdx.x;
+    uint32_t x[D];
+    bool alive = q < M;
+    if (alive) load_row<D>(surv_rows, q, x);
+    const long long qmax = min(M, q0 + kTriThreads);   // candidates live in [0, qmax - 1)
+    for (long long c0 = 0; c0 < qmax - 1; c0 += kTriChunk) {
+        const int cnt = (int)min((long long)kTriChunk, qmax - 1 - c0);
+        const uint4 *src = reinterpret_cast<const uint4 *>(surv_rows + c0 * DP);
+        uint4 *dst = reinterpret_cast<uint4 *>(chunk);
+        for (int v = threadIdx.x; v < cnt * DP / 4; v += kTriThreads) dst[v] = src[v];
+        __syncthreads();
+        if (alive) {
+            const long long lim = q - c0;
+            const int jend = (int)min((long long)cnt, lim < 0 ? 0 : lim);
+            for (int j = 0; j < jend; j++) {
+                uint32_t s[D];
+                load_row<D>(chunk, j, s);
+                if (dominates<D>(s, x)) { alive = false; break; }
+            }
+        }
+        if (!__syncthreads_or(alive)) break;
+    }
+    if (q < M && alive) skyflag[surv_orig[q]] = 1u;
+}
+
+__global__ void __launch_bounds__(kCT)
+k_count_flags(const uint32_t *flags, long long n, uint32_t *blocksum) {
+    uint32_t cnt = 0;
+    const long long b0 = (long long)blockIdx.x * kCB;
+    #pragma unroll
+    for (int r = 0; r < kPer; r++) {
+        const long long p = b0 + r * kCT + threadIdx.x;
+        if (p < n) cnt += flags[p];
+    }
+    uint32_t tot;
+    block_scan(cnt, &tot);
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+}
+
+// Skyline rows in ascending row order: row numbers and canonical rows.
+template <int D>
+__global__ void __launch_bounds__(kCT)
+k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyflag,
+              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows) {
+    uint32_t run = blocksum[blockIdx.x];
+    const long long b0 = (long long)blockIdx.x * kCB;
+    #pragma unroll 1
+    for (int r = 0; r < kPer; r++) {
+        const long long p = b0 + r * kCT + threadIdx.x;
+        const uint32_t f = p < n ? skyflag[p] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_scan(f, &tot);
+        if (f) {
+            sky_idx[run + ex] = p;
+            uint32_t x[D];
+            load_canon<D>(data, p, dir, x);
+            store_row<D>(sky_rows, run + ex, x);
+        }
+        run += tot;
+    }
+}
+
+template <int D>
+cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Workspace &ws,
+                      int64_t *d_sky_idx, cudaStream_t st) {
+    const long long nb = (n + kCB - 1) / kCB;
+    const int kb = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+    k_keys<D><<<kb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.vals[0], ws.hdr);
+    cudaError_t e = launch_radix_sort(ws, n, &ws.hdr->n_rows, 5, st);
+    if (e != cudaSuccess) return e;
+    k_reps<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps, ws.reps, ws.hdr);
+    k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.reps, ws.hdr,
+                                               ws.flags, ws.blocksum);
+    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv);
+    k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.flags,
+                                                     ws.blocksum, ws.surv_rows, ws.surv_orig, ws.hdr);
+    e = cudaMemsetAsync(ws.flags, 0, sizeof(uint32_t) * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    k_tri<D><<<(unsigned)((n + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(
+        ws.surv_rows, ws.surv_orig, ws.hdr, ws.flags);
+    k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum);
+    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky);
+    k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
+                                                    ws.sky_rows);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t scan_blocks(int64_t n) { return (n + kCB - 1) / kCB; }
+
+cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st) {
+    k_init<<<1, 32, 0, st>>>(ws.hdr, (long long)n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,
+                           Workspace &ws, int64_t *d_sky_idx, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    switch (d) {
+        case 1: return skyline_d<1>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 2: return skyline_d<2>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 3: return skyline_d<3>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 4: return skyline_d<4>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 5: return skyline_d<5>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 6: return skyline_d<6>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 7: return skyline_d<7>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 8: return skyline_d<8>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gres

@@ -1,0 +1,237 @@
+"""Thin Python binding of libgres (include/gres.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library. Device buffers are torch tensors (PyTorch provides
+device memory and streams); uint32 data travels as int32 tensors of the same
+bits. There is no CPU fallback: if the library cannot be built or loaded, or
+no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MIN, MAX = 0, 1
+PART_NONE, PART_GRID, PART_ANGULAR, PART_SLICED = 0, 1, 2, 3
+FLAG_COUNT_TESTS = 1
+
+_STATUS = {0: "GRES_OK", 1: "GRES_EINVAL", 2: "GRES_ENOMEM", 3: "GRES_EAGAIN",
+           4: "GRES_ETIMEOUT", 5: "GRES_ECUDA", 6: "GRES_EINTERNAL"}
+
+_lock = threading.Lock()
+_lib = None
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_u32 = ctypes.c_uint32
+_size = ctypes.c_size_t
+
+
+class GresError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanCfg(ctypes.Structure):
+    """``gres_plan_cfg``: candidate grouping and kernel shape (speed only)."""
+    _fields_ = [("scheme", _i32), ("m", _i32), ("p", _i32), ("slice_dim", _i32),
+                ("reps", _i32), ("slots", _i32), ("flags", _i32), ("reserved", _i32)]
+
+
+def plan(scheme: int = PART_GRID, m: int = 0, p: int = 0, slice_dim: int = 0, reps: int = 0,
+         slots: int = 0, count_tests: bool = False) -> PlanCfg:
+    return PlanCfg(scheme, m, p, slice_dim, reps, slots, FLAG_COUNT_TESTS if count_tests else 0, 0)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if needed) and load libgres; raise if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.gres_last_error.restype = ctypes.c_char_p
+        lib.gres_version.restype = ctypes.c_char_p
+        lib.gres_workspace_size.argtypes = [_i64, _i32, _i32, ctypes.POINTER(_size)]
+        lib.gres_workspace_size_host.argtypes = [_i64, _i32, _i32, ctypes.POINTER(_size)]
+        lib.sky_compute.argtypes = [_p, _i64, _i32, _i32, _p, _size, _p, _p, _p, _p]
+        lib.gres_compute.argtypes = [_p, _i64, _i32, _i32, _p, _i32, ctypes.POINTER(PlanCfg),
+                                     _p, _size, _p, _p, _p, _p, _p, _p]
+        lib.gres_compute_host.argtypes = [_p, _i64, _i32, _i32, _p, _i32, ctypes.POINTER(PlanCfg),
+                                          _p, _size, _p, _p, _p, _p]
+        lib.gres_gproj.argtypes = [_p, _i64, _p, _i32, _p, _p]
+        lib.gres_udiv_magic.argtypes = [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                                        ctypes.POINTER(_u32)]
+        for name in ("gres_workspace_size", "gres_workspace_size_host", "sky_compute",
+                     "gres_compute", "gres_compute_host", "gres_gproj", "gres_udiv_magic"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise GresError(status, load().gres_last_error().decode())
+
+
+def version() -> str:
+    return load().gres_version().decode()
+
+
+def workspace_size(n: int, d: int, k: int = 1, host: bool = False) -> int:
+    out = _size(0)
+    fn = load().gres_workspace_size_host if host else load().gres_workspace_size
+    _check(fn(int(n), int(d), int(k), ctypes.byref(out)))
+    return int(out.value)
+
+
+def udiv_magic(delta: int):
+    m, s1, s2 = _u32(0), _u32(0), _u32(0)
+    _check(load().gres_udiv_magic(int(delta), ctypes.byref(m), ctypes.byref(s1), ctypes.byref(s2)))
+    return int(m.value), int(s1.value), int(s2.value)
+
+
+# ---- torch-side helpers (device memory and streams) ---------------------------
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libgres needs a CUDA GPU; none is available")
+    return torch
+
+
+def to_device_u32(a, device="cuda"):
+    """numpy uint32 array -> contiguous int32 CUDA tensor holding the same bits."""
+    torch = _torch()
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _steps_array(steps) -> np.ndarray:
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.uint64))
+    if st.ndim != 1 or (st.size and (st.min() < 1 or st.max() > 0xFFFFFFFF)):
+        raise ValueError("steps must be a 1-D list of widths in [1, 2^32)")
+    return st.astype(np.uint32)
+
+
+@dataclass
+class Workspace:
+    tensor: object
+    nbytes: int
+
+
+def alloc_workspace(n: int, d: int, k: int = 1, host: bool = False) -> Workspace:
+    torch = _torch()
+    nbytes = workspace_size(n, d, k, host)
+    return Workspace(torch.empty(nbytes, dtype=torch.uint8, device="cuda"), nbytes)
+
+
+def sky_compute(data, direction: int = MIN, ws: Workspace | None = None, stream=None):
+    """Skyline row numbers (ascending int64 CUDA tensor) of an (n, d) int32/uint32 CUDA tensor."""
+    torch = _torch()
+    n, d = int(data.shape[0]), int(data.shape[1])
+    ws = ws or alloc_workspace(n, d, 1)
+    sky = torch.empty(max(n, 1), dtype=torch.int64, device=data.device)
+    cnt = ctypes.c_int64(0)
+    _check(load().sky_compute(_ptr(data), n, d, int(direction), _ptr(ws.tensor), ws.nbytes,
+                              _ptr(sky), None, ctypes.byref(cnt), _stream_ptr(stream)))
+    return sky[: cnt.value]
+
+
+def gres_compute(data, steps, direction: int = MIN, cfg: PlanCfg | None = None,
+                 ws: Workspace | None = None, stream=None, sync: bool = True,
+                 out=None, tests=None):
+    """Skyline and per-tuple first exit step.
+
+    ``data``: (n, d) int32 CUDA tensor (uint32 bits). Returns
+    ``(sky_idx[S], step_idx[S])`` CUDA tensors when ``sync`` (one host wait
+    for S); otherwise queues everything and returns ``(sky_idx, step_idx,
+    d_count)`` full-capacity tensors with S on the device (graph-capturable).
+    """
+    torch = _torch()
+    n, d = int(data.shape[0]), int(data.shape[1])
+    st = _steps_array(steps)
+    k = len(st)
+    ws = ws or alloc_workspace(n, d, k)
+    if out is None:
+        sky = torch.empty(max(n, 1), dtype=torch.int64, device=data.device)
+        res = torch.empty(max(n, 1), dtype=torch.int32, device=data.device)
+        dcnt = torch.zeros(1, dtype=torch.int64, device=data.device)
+    else:
+        sky, res, dcnt = out
+    cfgp = ctypes.byref(cfg) if cfg is not None else None
+    cnt = ctypes.c_int64(0)
+    _check(load().gres_compute(_ptr(data), n, d, int(direction),
+                               st.ctypes.data_as(ctypes.c_void_p), k, cfgp,
+                               _ptr(ws.tensor), ws.nbytes, _ptr(sky), _ptr(res), _ptr(dcnt),
+                               ctypes.byref(cnt) if sync else None, _ptr(tests),
+                               _stream_ptr(stream)))
+    if sync:
+        return sky[: cnt.value], res[: cnt.value]
+    return sky, res, dcnt
+
+
+def gres_compute_host(data_host, steps, direction: int = MIN, cfg: PlanCfg | None = None,
+                      ws: Workspace | None = None, stream=None, out=None):
+    """Host-buffer form: numpy (or pinned torch CPU) uint32 (n, d) in, numpy results out."""
+    torch = _torch()
+    if isinstance(data_host, np.ndarray):
+        a = np.ascontiguousarray(data_host, dtype=np.uint32)
+        n, d = a.shape
+        ptr = a.ctypes.data_as(ctypes.c_void_p)
+    else:
+        a = data_host
+        n, d = int(a.shape[0]), int(a.shape[1])
+        ptr = ctypes.c_void_p(a.data_ptr())
+    st = _steps_array(steps)
+    k = len(st)
+    ws = ws or alloc_workspace(n, d, k, host=True)
+    if out is None:
+        sky = np.empty(max(n, 1), dtype=np.int64)
+        res = np.empty(max(n, 1), dtype=np.int32)
+        sky_p, res_p = sky.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p)
+    else:
+        sky, res = out
+        sky_p, res_p = ctypes.c_void_p(sky.data_ptr()), ctypes.c_void_p(res.data_ptr())
+    cfgp = ctypes.byref(cfg) if cfg is not None else None
+    cnt = ctypes.c_int64(0)
+    _check(load().gres_compute_host(ptr, int(n), int(d), int(direction),
+                                    st.ctypes.data_as(ctypes.c_void_p), k, cfgp,
+                                    _ptr(ws.tensor), ws.nbytes, sky_p, res_p, ctypes.byref(cnt),
+                                    _stream_ptr(stream)))
+    return sky[: cnt.value], res[: cnt.value]
+
+
+def gproj(values, steps, stream=None):
+    """floor(values / steps[j]) for every width: a (k, count) int32 CUDA tensor (uint32 bits)."""
+    torch = _torch()
+    st = _steps_array(steps)
+    v = values if hasattr(values, "data_ptr") else to_device_u32(values)
+    count = int(v.numel())
+    out = torch.empty((len(st), max(count, 1)), dtype=torch.int32, device=v.device)
+    _check(load().gres_gproj(_ptr(v), count, st.ctypes.data_as(ctypes.c_void_p), len(st),
+                             _ptr(out), _stream_ptr(stream)))
+    return out[:, :count]
