@@ -1,0 +1,377 @@
+"""Benchmark: grid resistance (skyline + gres of every skyline tuple) on GB300.
+
+One step = one gres_compute call over a resident synthetic dataset: the
+sort-by-sum skyline pass, the candidate partitioning and the tile-pruned
+grid-dominance kernel. Default workload: anticorrelated N=100,000, d=4, values
+in [0, 2^20), 256 log-spaced integer widths 1 .. 2^16, Grid partitioning with
+m=4 slices per attribute.
+
+Metric: effective grid-dominance tests per second. Effective tests of one
+step = S * sum_t min(k*(t) + 1, K): the (candidate, width) tests of the plain
+early-exit scan of Algorithm 1 with the skyline as candidates (S candidates at
+each width up to the exit width). It depends only on the result.
+
+Prints one JSON line (rank 0). Timing: W warm-up steps; K timed steps, each
+bracketed by CUDA events on the launching stream, with a 256 MiB write
+flushing L2 between steps (outside the events); barrier + synchronize around
+the K steps; max over ranks. Under torchrun each rank runs its own dataset
+instance (seed = rank) on its own GPU: weak scaling, no collective on the
+data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2412_02274_gb300.inputs import make_dataset, steps_log, steps_linear  # noqa: E402
+
+# workload name -> (distribution, n, d, value bits, steps, partition scheme, m, p)
+WORKLOADS = {
+    "ant-n100000-d4-b20-k256-grid-m4": ("ant", 100_000, 4, 20, ("log", 256, 16), "grid", 4, 0),
+    "uni-n1000000-d6-b20-k256-angular-m2": ("uni", 1_000_000, 6, 20, ("log", 256, 16), "angular", 2, 0),
+    "uni-n1000000-d6-b20-k256-sliced-p64": ("uni", 1_000_000, 6, 20, ("log", 256, 16), "sliced", 0, 64),
+    "uni-n1000000-d6-b20-k256-none": ("uni", 1_000_000, 6, 20, ("log", 256, 16), "none", 0, 0),
+    "uni-n1000-d2-b16-k64-grid": ("uni", 1_000, 2, 16, ("lin", 64, 64), "grid", 0, 0),
+}
+DEFAULT_WORKLOAD = "ant-n100000-d4-b20-k256-grid-m4"
+SCHEMES = {"none": 0, "grid": 1, "angular": 2, "sliced": 3}
+METRIC = "effective grid-dominance tests/s (skyline + gres of every skyline tuple)"
+UNIT = "tests/s"
+
+
+def workload_inputs(name: str, seed: int):
+    dist, n, d, bits, st, scheme, m, p = WORKLOADS[name]
+    data = make_dataset(dist, n, d, bits=bits, seed=seed)
+    steps = steps_log(st[1], st[2]) if st[0] == "log" else steps_linear(st[1], st[2])
+    return data, steps, scheme, m, p
+
+
+def effective_tests(step_idx: np.ndarray, K: int) -> int:
+    S = len(step_idx)
+    return int(S) * int(np.minimum(step_idx.astype(np.int64) + 1, K).sum())
+
+
+# ---- clocks during the timed region --------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- roofline bookkeeping ----------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_2412_02274_gb300", "csrc", "gres_stage.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the dominance kernel from a committed ncu summary,
+    only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_dominance_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    h = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not h or not b or h.group(1) != kernel_source_hash():
+        return None
+    return float(b.group(1))
+
+
+# ---- the oracle on the host cores (baseline and reference arm) --------------------
+def oracle_rate(data, steps, sample: int, threads: int):
+    """Oracle effective tests/s: BNL skyline of the full dataset, then gres for a
+    fixed, evenly spaced sample of skyline tuples (all skyline tuples as
+    candidates); the gres time is scaled from the sample to all tuples."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    sky = O.skyline_bnl(data)
+    t_sky = time.perf_counter() - t0
+    S = len(sky)
+    take = min(sample, S)
+    targets = sky[np.linspace(0, S - 1, take).astype(np.int64)] if S else sky
+    t0 = time.perf_counter()
+    res = O.gres(data, steps, candidates=sky, targets=targets, threads=threads)
+    t_gres = time.perf_counter() - t0
+    K = len(steps)
+    scale = S / take if take else 0.0
+    eff = S * float(np.minimum(res.astype(np.int64) + 1, K).sum()) * scale
+    secs = t_sky + t_gres * scale
+    return {"value": eff / secs if secs > 0 else 0.0, "seconds_estimated_full": secs,
+            "seconds_run": t_sky + t_gres, "S": S, "sample_targets": take}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    data, steps, *_ = workload_inputs(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_rate(data, steps, args.ref_sample, threads)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = oracle_rate(data, steps, args.ref_sample, threads)
+        vals.append(r["value"])
+        secs += r["seconds_estimated_full"]
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"BNL skyline of all rows + gres of {r['sample_targets']} evenly "
+                                   f"spaced skyline tuples (of S={r['S']}), time scaled to all S"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- our arm ------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2412_02274_gb300 import gres as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+
+    data, steps, scheme, m, p = workload_inputs(args.workload, seed=rank)
+    n, d = data.shape
+    K = len(steps)
+    cfg = G.plan(SCHEMES[scheme], m=m, p=p)
+    x = G.to_device_u32(data, dev)
+    ws = G.alloc_workspace(n, d, K)
+    out = (torch.empty(n, dtype=torch.int64, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+           torch.zeros(1, dtype=torch.int64, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    for _ in range(args.warmup):
+        G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    S = int(out[2].item())
+    step_idx = out[1][:S].cpu().numpy()
+    eff = effective_tests(step_idx, K)
+
+    # executed (candidate, width) lane-tests of the dominance kernel: a separate counted run
+    tests = torch.zeros(1, dtype=torch.int64, device=dev)
+    cfg_c = G.plan(SCHEMES[scheme], m=m, p=p, count_tests=True)
+    G.gres_compute(x, steps, G.MIN, cfg_c, ws=ws, sync=False, out=out, stream=stream, tests=tests)
+    torch.cuda.synchronize(dev)
+    executed = int(tests.item())
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    G.timing_enable(True)
+    G.timing_read()
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = G.launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = G.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    stages = G.timing_read()
+    G.timing_enable(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    # result check: the timed steps produce the same result as the warm-up
+    assert int(out[2].item()) == S and np.array_equal(out[1][:S].cpu().numpy(), step_idx)
+
+    total_eff = float(eff) * args.steps
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([total_eff], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        total_eff = float(u.item())
+    value = total_eff / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the dominant kernel (the grid-dominance kernel)
+    dom_ms, dom_n = stages["dominance"]
+    dom_avg_s = (dom_ms / dom_n) / 1e3 if dom_n else None
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
+    alg_ops = executed * 2 * d           # 2d unsigned compares per (candidate, width) lane-test
+    achieved = alg_ops / dom_avg_s if dom_avg_s else 0.0
+    traffic = profiled_traffic(args.workload)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops if peak_ops else None,
+                "traffic": traffic,
+                "kernel": "k_dominance", "peak_basis": f"{props.multi_processor_count} SMs x 128 int32 "
+                f"lanes x {sm_max:.0f} MHz (max SM clock)",
+                "ops_per_launch": alg_ops, "avg_launch_ms": dom_avg_s * 1e3 if dom_avg_s else None}
+
+    # end to end through the host-buffer ABI: pinned input, H2D + compute + D2H each step
+    pinned = torch.from_numpy(data.view(np.int32)).pin_memory()
+    ws_h = G.alloc_workspace(n, d, K, host=True)
+    hs = torch.empty(n, dtype=torch.int64).pin_memory()
+    hr = torch.empty(n, dtype=torch.int32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        G.gres_compute_host(pinned, steps, G.MIN, cfg, ws=ws_h, out=(hs, hr), stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sk, rr = G.gres_compute_host(pinned, steps, G.MIN, cfg, ws=ws_h, out=(hs, hr), stream=stream)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    assert np.array_equal(rr.numpy(), step_idx)
+    e2e_s_all = e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s_all = float(t.item())
+    e2e = {"value": total_eff / args.steps / e2e_s_all, "unit": UNIT,
+           "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(S * 12 + 8),
+           "ms_per_step": e2e_s_all * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r = oracle_rate(data, steps, args.cpu_sample, threads)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"BNL skyline of all {n} rows + gres of {r['sample_targets']} evenly spaced "
+                         f"skyline tuples (of S={r['S']}) against all S, gres time scaled to all S; "
+                         f"{r['seconds_run']:.1f} s of CPU wall time"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": int(n), "d": int(d), "value_bits": WORKLOADS[args.workload][3],
+                       "widths": K, "scheme": scheme, "m": m, "p": p, "skyline_size": S,
+                       "effective_tests_per_step": eff, "executed_lane_tests_per_step": executed,
+                       "l2": "256 MiB write between timed steps", "seed_per_rank": "rank",
+                       "parallelism": f"replicas x{world} (one dataset per GPU)"},
+            "gres_queries_per_s": world * 1e3 / ms_per_step,
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--ref-sample", type=int, default=512)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -165,6 +165,22 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
 gres_status gres_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps,
                        int32_t k, uint32_t *d_out, void *stream);
 
+/* Number of CUDA kernels this library has queued since it was loaded (all
+ * threads). For accounting in benchmarks. */
+unsigned long long gres_launch_count(void);
+
+/* Per-stage device timing for benchmarks. While enabled on the calling
+ * thread, sky_compute and gres_compute record a pair of CUDA events on the
+ * caller's stream around each stage: 0 = skyline pass, 1 = candidate
+ * partitioning (range, partition keys, sort, tiles), 2 = the grid-dominance
+ * kernel. gres_timing_enable(on) turns recording on or off and clears the
+ * record. gres_timing_read waits for the recorded events and writes, for
+ * stages 0 .. nstages-1, the summed milliseconds ms[i] and the number of
+ * timed intervals launches[i], then clears the record. Events are created on
+ * first use (do a warm-up call before timing) and reused afterwards. */
+gres_status gres_timing_enable(int32_t on);
+gres_status gres_timing_read(double *ms, int64_t *launches, int32_t nstages);
+
 /* Host helper: the multiply-high constants gres_gproj uses for divisor
  * `delta` (>= 1): floor(v / delta) = (t + ((v - t) >> s1)) >> s2 with
  * t = mulhi(m, v). Exposed so the constants can be checked without a GPU. */

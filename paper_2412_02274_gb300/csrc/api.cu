@@ -4,13 +4,35 @@
 // gres_stage.cu); nothing here computes a result on the host.
 #include "gres_internal.cuh"
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_launches{0};
+
+// Per-thread stage timer: CUDA event pairs recorded on the launching stream.
+struct StageTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Pair { int stage; cudaEvent_t a, b; };
+    std::vector<Pair> pairs;
+    cudaEvent_t open[gres::kStageCount] = {};
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+};
+thread_local StageTimer g_timer;
 
 gres_status fail(gres_status s, const std::string &msg) {
     g_last_error = msg;
@@ -64,6 +86,7 @@ gres_status check_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *out) 
                 m++;
             }
             c.m = dims > 0 ? m : 1;
+            if (c.scheme == GRES_PART_ANGULAR && c.m > 64) c.m = 64;
         }
         if (c.m < 1) return fail(GRES_EINVAL, "cfg.m must be >= 1");
         double cells = 1.0;
@@ -116,6 +139,25 @@ gres_status finish_counts(gres::Workspace &ws, int64_t *d_sky_count, int64_t *h_
 
 namespace gres {
 
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void stage_begin(int stage, cudaStream_t st) {
+    if (!g_timer.on) return;
+    cudaEvent_t e = g_timer.next();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    g_timer.open[stage] = e;
+}
+
+void stage_end(int stage, cudaStream_t st) {
+    if (!g_timer.on || !g_timer.open[stage]) return;
+    cudaEvent_t e = g_timer.next();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    g_timer.pairs.push_back({stage, g_timer.open[stage], e});
+    g_timer.open[stage] = nullptr;
+}
+
 size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     const int DP = padded_dims(d);
     const int64_t nn = n > 0 ? n : 1;
@@ -160,6 +202,32 @@ const char *gres_last_error(void) { return g_last_error.c_str(); }
 
 const char *gres_version(void) { return "libgres 0.1 (sm_103a)"; }
 
+unsigned long long gres_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+gres_status gres_timing_enable(int32_t on) {
+    g_timer.on = on != 0;
+    g_timer.pairs.clear();
+    g_timer.used = 0;
+    for (auto &e : g_timer.open) e = nullptr;
+    return GRES_OK;
+}
+
+gres_status gres_timing_read(double *ms, int64_t *launches, int32_t nstages) {
+    if (!ms || !launches || nstages < 1) return fail(GRES_EINVAL, "bad timing outputs");
+    for (int i = 0; i < nstages; i++) { ms[i] = 0.0; launches[i] = 0; }
+    for (const auto &p : g_timer.pairs) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, p.a, p.b);
+        if (e != cudaSuccess) return cuda_fail(e, "timing event");
+        if (p.stage < nstages) { ms[p.stage] += t; launches[p.stage] += 1; }
+    }
+    g_timer.pairs.clear();
+    g_timer.used = 0;
+    return GRES_OK;
+}
+
 gres_status gres_workspace_size(int64_t n, int32_t d, int32_t k, size_t *bytes) {
     if (!bytes) return fail(GRES_EINVAL, "bytes is NULL");
     gres_status s = check_dims(n, d);
@@ -192,7 +260,9 @@ gres_status sky_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t di
     gres::workspace_layout(n, d, 1, d_ws, &ws);
     cudaError_t e = gres::launch_init(ws, n, st);
     if (e != cudaSuccess) return cuda_fail(e, "init");
+    gres::stage_begin(gres::kStageSkyline, st);
     e = gres::launch_skyline(d_data, n, d, dir, gres::kMaxReps, ws, d_sky_idx, st);
+    gres::stage_end(gres::kStageSkyline, st);
     if (e != cudaSuccess) return cuda_fail(e, "skyline");
     return finish_counts(ws, d_sky_count, h_sky_count, st);
 }
@@ -222,7 +292,9 @@ gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t d
     if (e != cudaSuccess) return cuda_fail(e, "init");
     e = gres::launch_upload_steps(ws, h_steps, k, st);
     if (e != cudaSuccess) return cuda_fail(e, "steps upload");
+    gres::stage_begin(gres::kStageSkyline, st);
     e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st);
+    gres::stage_end(gres::kStageSkyline, st);
     if (e != cudaSuccess) return cuda_fail(e, "skyline");
     e = gres::launch_gres_stage(d_data, n, d, dir, k, plan, ws, d_sky_idx, d_step_idx, d_tests, st);
     if (e != cudaSuccess) return cuda_fail(e, "gres stage");

@@ -90,6 +90,15 @@ __device__ __forceinline__ uint32_t udiv(uint32_t v, uint32_t m, uint32_t s1, ui
 // Canonical value: smaller is better after this map (GRES_MAX reads ~v).
 __device__ __forceinline__ uint32_t canon(uint32_t v, int dir) { return dir ? ~v : v; }
 
+// Counts kernel launches queued by the library (gres_launch_count()).
+void note_launch();
+
+// Optional per-stage timing with CUDA events on the launching stream
+// (gres_timing_enable / gres_timing_read). Stage ids:
+enum Stage { kStageSkyline = 0, kStagePartition = 1, kStageDominance = 2, kStageCount = 3 };
+void stage_begin(int stage, cudaStream_t st);
+void stage_end(int stage, cudaStream_t st);
+
 // ---- kernel launchers (each queues on `st`, returns the launch error) -------
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
 cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, cudaStream_t st);

@@ -514,7 +514,7 @@ cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
         configured = true;
     }
     a.smem_words = smem / 4;
-    k_dominance<D, SLOTS><<<g_sm_count, dom_threads<D>(), smem, st>>>(a);
+    k_dominance<D, SLOTS><<<g_sm_count, dom_threads<D>(), smem, st>>>(a); note_launch();
     return cudaGetLastError();
 }
 
@@ -522,7 +522,8 @@ template <int D, int SLOTS>
 cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Workspace &ws,
                           int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
     const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count * 4);
-    k_sky_range<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr);
+    stage_begin(kStagePartition, st);
+    k_sky_range<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr); note_launch();
     const int scheme = cfg.scheme;
     PartArgs pa;
     std::memset(&pa, 0, sizeof(pa));
@@ -540,19 +541,20 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     }
     cudaError_t e;
     if (scheme != GRES_PART_NONE) {
-        k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]);
+        k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]); note_launch();
         e = launch_radix_sort(ws, n, &ws.hdr->n_sky, 8, st);
         if (e != cudaSuccess) return e;
         if (scheme == GRES_PART_SLICED) {
-            k_reset_keyrange<<<1, 1, 0, st>>>(ws.hdr);
-            k_sliced_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0], ws.vals[1]);
+            k_reset_keyrange<<<1, 1, 0, st>>>(ws.hdr); note_launch();
+            k_sliced_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0], ws.vals[1]); note_launch();
             e = launch_radix_sort(ws, n, &ws.hdr->n_sky, 8, st);
             if (e != cudaSuccess) return e;
         }
     }
     const int pb = (int)std::min<int64_t>((n + 255) / 256 + 1, (int64_t)g_sm_count * 8);
     k_permute<D><<<pb, 256, 0, st>>>(ws.sky_rows, ws.vals[0], ws.vals[1], ws.hdr,
-                                     scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.perm);
+                                     scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.perm); note_launch();
+    stage_end(kStagePartition, st);
     DomArgs a;
     a.cand = ws.cand;
     a.tmin = ws.tmin;
@@ -563,9 +565,11 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     a.K = k;
     a.dir = dir;
     a.smem_words = 0;
+    stage_begin(kStageDominance, st);
     e = launch_dom<D, SLOTS>(a, st);
+    stage_end(kStageDominance, st);
     if (e != cudaSuccess) return e;
-    k_scatter_res<<<pb, 256, 0, st>>>(ws.res, ws.perm, ws.hdr, d_step_idx);
+    k_scatter_res<<<pb, 256, 0, st>>>(ws.res, ws.perm, ws.hdr, d_step_idx); note_launch();
     return cudaGetLastError();
 }
 
@@ -588,7 +592,7 @@ cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, c
             udiv_magic(h_steps[off + i], &m, &s1, &s2);
             c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
         }
-        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic);
+        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic); note_launch();
     }
     return cudaGetLastError();
 }
@@ -629,7 +633,7 @@ cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t
         }
         const long long total = (long long)count * c.count;
         const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g_sm_count * 8);
-        k_gproj<<<blocks, 256, 0, st>>>(d_values, (long long)count, c, d_out);
+        k_gproj<<<blocks, 256, 0, st>>>(d_values, (long long)count, c, d_out); note_launch();
     }
     return cudaGetLastError();
 }

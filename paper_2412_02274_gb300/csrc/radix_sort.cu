@@ -155,17 +155,17 @@ cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n
                               int max_passes, cudaStream_t st) {
     const int64_t G = sort_blocks(n_max);
     if (G == 0) {
-        k_sort_done<<<1, 1, 0, st>>>(ws.hdr);
+        k_sort_done<<<1, 1, 0, st>>>(ws.hdr); note_launch();
         return cudaGetLastError();
     }
     for (int p = 0; p < max_passes; p++) {
         const int in = p & 1, out = (p + 1) & 1;
-        k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p);
-        k_scan<<<1, kScanThreads, 0, st>>>(ws.hdr, ws.hist, d_n, p);
+        k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p); note_launch();
+        k_scan<<<1, kScanThreads, 0, st>>>(ws.hdr, ws.hist, d_n, p); note_launch();
         k_scatter<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.vals[in], ws.keys[out],
-                                                    ws.vals[out], ws.hist, d_n, p);
+                                                    ws.vals[out], ws.hist, d_n, p); note_launch();
     }
-    k_sort_done<<<1, 1, 0, st>>>(ws.hdr);
+    k_sort_done<<<1, 1, 0, st>>>(ws.hdr); note_launch();
     return cudaGetLastError();
 }
 

@@ -370,23 +370,23 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
                       int64_t *d_sky_idx, cudaStream_t st) {
     const long long nb = (n + kCB - 1) / kCB;
     const int kb = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
-    k_keys<D><<<kb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.vals[0], ws.hdr);
+    k_keys<D><<<kb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.vals[0], ws.hdr); note_launch();
     cudaError_t e = launch_radix_sort(ws, n, &ws.hdr->n_rows, 5, st);
     if (e != cudaSuccess) return e;
-    k_reps<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps, ws.reps, ws.hdr);
+    k_reps<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps, ws.reps, ws.hdr); note_launch();
     k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.reps, ws.hdr,
-                                               ws.flags, ws.blocksum);
-    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv);
+                                               ws.flags, ws.blocksum); note_launch();
+    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv); note_launch();
     k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.flags,
-                                                     ws.blocksum, ws.surv_rows, ws.surv_orig, ws.hdr);
+                                                     ws.blocksum, ws.surv_rows, ws.surv_orig, ws.hdr); note_launch();
     e = cudaMemsetAsync(ws.flags, 0, sizeof(uint32_t) * (size_t)n, st);
     if (e != cudaSuccess) return e;
     k_tri<D><<<(unsigned)((n + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(
-        ws.surv_rows, ws.surv_orig, ws.hdr, ws.flags);
-    k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum);
-    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky);
+        ws.surv_rows, ws.surv_orig, ws.hdr, ws.flags); note_launch();
+    k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum); note_launch();
+    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky); note_launch();
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
-                                                    ws.sky_rows);
+                                                    ws.sky_rows); note_launch();
     return cudaGetLastError();
 }
 
@@ -395,7 +395,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
 int64_t scan_blocks(int64_t n) { return (n + kCB - 1) / kCB; }
 
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st) {
-    k_init<<<1, 32, 0, st>>>(ws.hdr, (long long)n);
+    k_init<<<1, 32, 0, st>>>(ws.hdr, (long long)n); note_launch();
     return cudaGetLastError();
 }
 

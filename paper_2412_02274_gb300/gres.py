@@ -75,8 +75,13 @@ def load():
         lib.gres_gproj.argtypes = [_p, _i64, _p, _i32, _p, _p]
         lib.gres_udiv_magic.argtypes = [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                                         ctypes.POINTER(_u32)]
+        lib.gres_launch_count.restype = ctypes.c_ulonglong
+        lib.gres_launch_count.argtypes = []
+        lib.gres_timing_enable.argtypes = [_i32]
+        lib.gres_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
         for name in ("gres_workspace_size", "gres_workspace_size_host", "sky_compute",
-                     "gres_compute", "gres_compute_host", "gres_gproj", "gres_udiv_magic"):
+                     "gres_compute", "gres_compute_host", "gres_gproj", "gres_udiv_magic",
+                     "gres_timing_enable", "gres_timing_read"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -96,6 +101,26 @@ def workspace_size(n: int, d: int, k: int = 1, host: bool = False) -> int:
     fn = load().gres_workspace_size_host if host else load().gres_workspace_size
     _check(fn(int(n), int(d), int(k), ctypes.byref(out)))
     return int(out.value)
+
+
+STAGES = ("skyline", "partition", "dominance")
+
+
+def launch_count() -> int:
+    """Kernels queued by libgres since it was loaded."""
+    return int(load().gres_launch_count())
+
+
+def timing_enable(on: bool = True) -> None:
+    _check(load().gres_timing_enable(1 if on else 0))
+
+
+def timing_read() -> dict:
+    """{stage: (summed ms, intervals)} for the events recorded since the last read."""
+    ms = (ctypes.c_double * len(STAGES))()
+    n = (_i64 * len(STAGES))()
+    _check(load().gres_timing_read(ms, n, len(STAGES)))
+    return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(STAGES)}
 
 
 def udiv_magic(delta: int):
