@@ -181,6 +181,29 @@ unsigned long long gres_launch_count(void);
 gres_status gres_timing_enable(int32_t on);
 gres_status gres_timing_read(double *ms, int64_t *launches, int32_t nstages);
 
+/* gres_compute without a caller workspace. The paper has no counterpart: this
+ * exists for callers that cannot allocate device memory when they need a
+ * result -- e.g. a plugin on another framework's stream whose allocator owns
+ * the free memory, or a latency-critical loop that must not call cudaMalloc
+ * (it can synchronize the device) -- and so cannot provide d_ws.
+ * Same arguments and results as gres_compute, minus d_ws/ws_bytes/d_tests.
+ * Scratch: one static device array of gres_static_scratch_bytes() bytes
+ * (16 MiB: about 190,000 rows at d <= 4, 120,000 at d = 8, with up to 4,096
+ * widths) inside the library, held on every GPU that loads the library until
+ * the process exits. Sizes whose gres_workspace_size exceeds it give
+ * GRES_EINVAL and nothing is launched. The call allocates nothing (no
+ * cudaMalloc / cudaFree); keep gres_timing_enable off, since stage timing
+ * creates CUDA events on first use. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture. All calls share the array:
+ * each call re-initialises what it needs, and calls that overlap on the GPU
+ * (different streams or unsynchronised threads) race on it -- serialise them. */
+gres_status gres_compute_static(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,
+                                const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
+                                int64_t *d_sky_idx, int32_t *d_step_idx,
+                                int64_t *d_sky_count, int64_t *h_sky_count, void *stream);
+size_t gres_static_scratch_bytes(void);
+
 /* Host helper: the multiply-high constants gres_gproj uses for divisor
  * `delta` (>= 1): floor(v / delta) = (t + ((v - t) >> s1)) >> s2 with
  * t = mulhi(m, v). Exposed so the constants can be checked without a GPU. */

@@ -139,6 +139,8 @@ gres_status finish_counts(gres::Workspace &ws, int64_t *d_sky_count, int64_t *h_
 
 namespace gres {
 
+gres_status set_error(gres_status s, const char *msg) { return fail(s, msg); }
+
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void stage_begin(int stage, cudaStream_t st) {

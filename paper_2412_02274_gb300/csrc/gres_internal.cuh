@@ -90,6 +90,9 @@ __device__ __forceinline__ uint32_t udiv(uint32_t v, uint32_t m, uint32_t s1, ui
 // Canonical value: smaller is better after this map (GRES_MAX reads ~v).
 __device__ __forceinline__ uint32_t canon(uint32_t v, int dir) { return dir ? ~v : v; }
 
+// Sets the calling thread's gres_last_error() message; returns s.
+gres_status set_error(gres_status s, const char *msg);
+
 // Counts kernel launches queued by the library (gres_launch_count()).
 void note_launch();
 
