@@ -239,11 +239,11 @@ def run_ours(args):
     eff = effective_tests(step_idx, K)
 
     # executed (candidate, width) lane-tests of the dominance kernel: a separate counted run
-    tests = torch.zeros(1, dtype=torch.int64, device=dev)
+    tests = torch.zeros(2, dtype=torch.int64, device=dev)
     cfg_c = G.plan(SCHEMES[scheme], m=m, p=p, count_tests=True)
     G.gres_compute(x, steps, G.MIN, cfg_c, ws=ws, sync=False, out=out, stream=stream, tests=tests)
     torch.cuda.synchronize(dev)
-    executed = int(tests.item())
+    executed, checks = (int(v) for v in tests.cpu().tolist())
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -290,7 +290,8 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
     peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
-    alg_ops = executed * 2 * d           # 2d unsigned compares per (candidate, width) lane-test
+    # 2d unsigned compares per (candidate, width) lane-test and per pruning check
+    alg_ops = (executed + checks) * 2 * d
     achieved = alg_ops / dom_avg_s if dom_avg_s else 0.0
     traffic = profiled_traffic(args.workload)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -339,6 +340,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "n": int(n), "d": int(d), "value_bits": WORKLOADS[args.workload][3],
                        "widths": K, "scheme": scheme, "m": m, "p": p, "skyline_size": S,
                        "effective_tests_per_step": eff, "executed_lane_tests_per_step": executed,
+                       "pruning_checks_per_step": checks,
                        "l2": "256 MiB write between timed steps", "seed_per_rank": "rank",
                        "parallelism": f"replicas x{world} (one dataset per GPU)"},
             "gres_queries_per_s": world * 1e3 / ms_per_step,

@@ -90,8 +90,8 @@ typedef struct {
     int32_t reserved;     /* must be 0                                                  */
 } gres_plan_cfg;
 
-/* Count the (candidate, step) dominance tests the gres kernel evaluates into
- * d_tests (see gres_compute). Slower; for accounting only. */
+/* Count the dominance tests and pruning checks the gres kernel evaluates into
+ * d_tests (see gres_compute). For accounting only. */
 #define GRES_FLAG_COUNT_TESTS 1
 
 /* Thread-local message for the calling thread's most recent failed call
@@ -131,8 +131,11 @@ gres_status sky_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t di
  *   d_step_idx   device, capacity n int32: result per skyline row, in [0, k]
  *   d_sky_count  device int64 (may be NULL): S
  *   h_sky_count  host int64 (may be NULL): S; waits for the stream
- *   d_tests      device uint64 (may be NULL): with GRES_FLAG_COUNT_TESTS, the
- *                number of (candidate, step) tests evaluated, added to *d_tests
+ *   d_tests      device uint64[2] (may be NULL): with GRES_FLAG_COUNT_TESTS,
+ *                [0] += (candidate, step) tests evaluated by the grid-dominance
+ *                kernel, counted per lane (32 per warp-wide test of one
+ *                candidate row at 32 steps), [1] += pruning checks (one per
+ *                tile bounding box or candidate row looked at, per lane)
  * With h_sky_count == NULL nothing waits on the host, so the call can be
  * captured into a CUDA graph (all sizes after the skyline live on the device). */
 gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,

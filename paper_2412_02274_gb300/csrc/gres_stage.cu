@@ -26,10 +26,16 @@
 //     dominator (the minimum over steps, Def. 2); steps are never bisected
 //     since membership is not monotone in the width.
 //
-// Mapping: one warp per target tuple (dynamic queue). Lane l holds the
-// bounds of steps w0 + 32 j + l (j < SLOTS) in registers; every candidate
-// row of a tile is broadcast to all lanes; a ballot per slot and __ffs give
-// the first dominated step. The candidate rows and tile minima are staged in
+//   * inside a tile, each row s gets its own first relevant step
+//     (delta > max_i (s_i - t_i)^+); rows whose first relevant step is not
+//     before the best step found so far are never tested, and the others are
+//     tested only from that step on, in ascending order of it.
+//
+// Mapping: one warp per target tuple (dynamic queue). Lanes scan 32 tiles at
+// a time, then the 32 rows of a chosen tile. Lane l holds the bounds of steps
+// w0 + 32 j + l (j < SLOTS) in registers, computed on first use of slot j; a
+// row to test is shuffled to all lanes; a ballot per slot and __ffs give the
+// first dominated step. The candidate rows and tile minima are staged in
 // shared memory with cp.async when they fit (they do for skylines up to
 // about 6,900 rows at d = 6), otherwise read through L1.
 #include "gres_internal.cuh"
@@ -168,13 +174,21 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&x)[D], int q) {
     return v;
 }
 
+// Order inside a partition: attribute `sec` of x = v - lo, scaled to 16 bits
+// of its range (so that a sort key stays within 32 bits for up to 2^16 cells).
+template <int D>
+__device__ __forceinline__ unsigned long long sec16(const uint32_t (&x)[D], const WsHeader *h, int sec) {
+    const unsigned long long span = (unsigned long long)(h->hi[sec] - h->lo[sec]) + 1ull;
+    return ((unsigned long long)pick<D>(x, sec) << 16) / span;
+}
+
 // Partition numbers (Sec. 3.1) on coordinates x = v - lo (canonical):
 //   GRID:    c_i = floor(x_i m / (hi_i - lo_i + 1)), p = sum_i c_i m^i
 //   ANGULAR: phi_i = atan2(sqrt(sum_{j>i} x_j^2), x_i); bin_i = number of
 //            thresholds j pi / 2m reached, decided exactly as
 //            (Y << 32) >= X * thr_j in 128-bit integers (Eq. 1)
 //   SLICED:  first pass keys on x_dim; the slice comes from the rank.
-// Sort key = partition << 32 | x_sec (order inside a partition), value = row.
+// Sort key = partition << 16 | sec16 (order inside a partition), value = row.
 template <int D>
 __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                             unsigned long long *keys, uint32_t *vals) {
@@ -200,7 +214,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                     pid += ((unsigned long long)x[i] * (unsigned long long)a.m) / span * w;
                     w *= (unsigned long long)a.m;
                 }
-                key = (pid << 32) | pick<D>(x, a.sec);
+                key = (pid << 16) | sec16(x, h, a.sec);
             } else if (a.scheme == GRES_PART_ANGULAR) {
                 unsigned long long w = 1;
                 #pragma unroll
@@ -217,7 +231,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                     pid += (unsigned long long)bin * w;
                     w *= (unsigned long long)a.m;
                 }
-                key = (pid << 32) | pick<D>(x, a.sec);
+                key = (pid << 16) | sec16(x, h, a.sec);
             } else {  // SLICED, first pass
                 key = pick<D>(x, a.dim);
             }
@@ -232,7 +246,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
 
 // SLICED second pass (after k_reset_keyrange): the row of rank r in the
 // order of x_dim falls in slice floor(r p / S) (Sec. 3.1); the new key orders
-// rows by (slice, x_sec). Reads the sorted buffer, writes buffer 0 at the same
+// rows by (slice, sec16). Reads the sorted buffer, writes buffer 0 at the same
 // index (in place when the sorted buffer is buffer 0).
 template <int D>
 __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
@@ -251,7 +265,10 @@ __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
             ld_row<D>(sky_rows, j, x);
             const unsigned long long slice =
                 (unsigned long long)r * (unsigned long long)a.p / (unsigned long long)S;
-            key = (slice << 32) | (unsigned long long)(pick<D>(x, a.sec) - h->lo[a.sec]);
+            uint32_t xr[D];
+            #pragma unroll
+            for (int q = 0; q < D; q++) xr[q] = x[q] - h->lo[q];
+            key = (slice << 16) | sec16(xr, h, a.sec);
         }
         if (valid) {
             keys0[r] = key;
@@ -312,6 +329,7 @@ struct DomArgs {
     const uint32_t *cand;     // T*32 rows, DP words each (partition order)
     const uint32_t *tmin;     // T rows, DP words each
     const uint32_t *magic;    // K * 4: (m, s1, s2, delta)
+    const uint32_t *steps;    // K widths
     WsHeader *hdr;
     int32_t *res;             // per partition position
     unsigned long long *tests;
@@ -331,13 +349,23 @@ __host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 
 constexpr int kTileKeys = 8;                 // tile keys per lane in one selection round
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
+// First index in ws[0 .. n) whose width exceeds e (ws ascending).
+__device__ __forceinline__ int first_wider(const uint32_t *ws, int n, uint32_t e) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ws[mid] <= e) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 template <int D, int SLOTS, bool RES>
 __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *cand, const uint32_t *tmin,
                                               uint32_t *wsteps, long long S, long long T) {
     constexpr int WS = 32 * SLOTS;
     const int lane = threadIdx.x & 31;
     const int K = a.K;
-    unsigned long long my_tests = 0;
+    unsigned long long n_tests = 0, n_checks = 0;
     for (;;) {
         unsigned i = 0;
         if (lane == 0) i = atomicAdd(&a.hdr->work_next, 1u);
@@ -348,31 +376,18 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
         int result = K;
         for (int w0 = 0; w0 < K; w0 += WS) {
             const int wcount = min(WS, K - w0);
-            uint32_t U[SLOTS][D], L[SLOTS][D];
+            // this window's widths in shared memory; bounds are made on first use
             #pragma unroll
             for (int j = 0; j < SLOTS; j++) {
                 const int k = w0 + 32 * j + lane;
-                if (k < K) {
-                    const uint4 mg = __ldg(reinterpret_cast<const uint4 *>(a.magic) + k);
-                    const uint32_t delta = mg.w;
-                    wsteps[32 * j + lane] = delta;
-                    #pragma unroll
-                    for (int q = 0; q < D; q++) {
-                        const uint32_t v = a.dir ? ~t[q] : t[q];
-                        const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
-                        const uint32_t uv = lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
-                        U[j][q] = a.dir ? ~lv : uv;
-                        L[j][q] = a.dir ? ~uv : lv;
-                    }
-                } else {
-                    wsteps[32 * j + lane] = 0xFFFFFFFFu;
-                    #pragma unroll
-                    for (int q = 0; q < D; q++) { U[j][q] = 0u; L[j][q] = 0u; }
-                }
+                wsteps[32 * j + lane] = k < K ? __ldg(a.steps + k) : 0xFFFFFFFFu;
             }
             __syncwarp();
+            uint32_t U[SLOTS][D], L[SLOTS][D];
+            unsigned ready = 0;   // slots whose bounds are in U, L
             int best = wcount;
             for (long long tc = 0; tc < T && best > 0; tc += 32 * kTileKeys) {
+                // tile level: first width at which a tile can hold a dominator
                 uint32_t key[kTileKeys];
                 #pragma unroll
                 for (int e = 0; e < kTileKeys; e++) {
@@ -389,49 +404,78 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
                             can |= mn[q] < t[q];
                         }
                         if (can) {
-                            int lo = 0, hi = wcount;   // first window step with delta > emax
-                            while (lo < hi) {
-                                const int mid = (lo + hi) >> 1;
-                                if (wsteps[mid] <= emax) lo = mid + 1; else hi = mid;
-                            }
+                            const int lo = first_wider(wsteps, best, emax);
                             if (lo < best) key[e] = ((uint32_t)lo << 16) | (uint32_t)(32 * e + lane);
                         }
                     }
                 }
+                n_checks += 32 * kTileKeys;
                 for (;;) {
                     uint32_t lm = key[0];
                     #pragma unroll
                     for (int e = 1; e < kTileKeys; e++) lm = min(lm, key[e]);
                     const uint32_t mkey = __reduce_min_sync(kFull, lm);
-                    if (mkey == kNoTile) break;
-                    const int klo = (int)(mkey >> 16);
-                    if (klo >= best) break;
+                    if (mkey == kNoTile || (int)(mkey >> 16) >= best) break;
                     #pragma unroll
                     for (int e = 0; e < kTileKeys; e++) key[e] = key[e] == mkey ? kNoTile : key[e];
-                    const long long tile = tc + (mkey & 0xFFFFu);
-                    const int jlo = klo >> 5, jhi = (best - 1) >> 5;
-                    const long long r0 = tile * kTileRows;
+                    const long long r0 = (tc + (mkey & 0xFFFFu)) * kTileRows;
+                    // candidate level: lane r looks at row r of the tile
+                    uint32_t s[D];
+                    if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
+                    uint32_t e_r = 0;
+                    bool can_r = false;
                     #pragma unroll
-                    for (int j = 0; j < SLOTS; j++) {
-                        if (j < jlo || j > jhi) continue;
-                        bool hit = false;
-                        #pragma unroll 8
-                        for (int r = 0; r < kTileRows; r++) {
-                            uint32_t s[D];
-                            if (RES) ld_row<D>(cand, r0 + r, s); else ldg_row<D>(cand, r0 + r, s);
+                    for (int q = 0; q < D; q++) {
+                        e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
+                        can_r |= s[q] < t[q];
+                    }
+                    n_checks += 32;
+                    // a row can dominate t first at its first width wider than e_r;
+                    // it matters only if that width comes before best
+                    uint32_t ckey = 0xFFFFFFFFu;
+                    if (can_r && e_r < wsteps[best - 1])
+                        ckey = ((uint32_t)first_wider(wsteps, best, e_r) << 5) | (uint32_t)lane;
+                    for (;;) {
+                        const uint32_t ck = __reduce_min_sync(kFull, ckey);
+                        if (ck == 0xFFFFFFFFu || (int)(ck >> 5) >= best) break;
+                        const int c = (int)(ck & 31u);
+                        if (lane == c) ckey = 0xFFFFFFFFu;
+                        uint32_t sc[D];
+                        #pragma unroll
+                        for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
+                        const int jlo = (int)(ck >> 5) >> 5, jhi = (best - 1) >> 5;
+                        #pragma unroll
+                        for (int j = 0; j < SLOTS; j++) {
+                            if (j < jlo || j > jhi) continue;
+                            if (!(ready & (1u << j))) {
+                                ready |= 1u << j;
+                                const int k = w0 + 32 * j + lane;
+                                const bool live = k < K;
+                                const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(a.magic) + k)
+                                                      : make_uint4(1u, 0u, 0u, 1u);
+                                const uint32_t delta = mg.w;
+                                #pragma unroll
+                                for (int q = 0; q < D; q++) {
+                                    const uint32_t v = a.dir ? ~t[q] : t[q];
+                                    const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
+                                    const uint32_t uv =
+                                        lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+                                    U[j][q] = live ? (a.dir ? ~lv : uv) : 0u;
+                                    L[j][q] = live ? (a.dir ? ~uv : lv) : 0u;
+                                }
+                            }
                             bool le = true, lt = false;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                le &= s[q] <= U[j][q];
-                                lt |= s[q] < L[j][q];
+                                le &= sc[q] <= U[j][q];
+                                lt |= sc[q] < L[j][q];
                             }
-                            hit |= le & lt;
-                        }
-                        my_tests += kTileRows * 32;
-                        const unsigned msk = __ballot_sync(kFull, hit);
-                        if (msk) {
-                            best = min(best, 32 * j + __ffs(msk) - 1);
-                            break;
+                            n_tests += 32;
+                            const unsigned msk = __ballot_sync(kFull, le & lt);
+                            if (msk) {
+                                best = min(best, 32 * j + __ffs(msk) - 1);
+                                break;
+                            }
                         }
                     }
                 }
@@ -441,7 +485,10 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
         }
         if (lane == 0) a.res[i] = result;
     }
-    if (a.tests && lane == 0 && my_tests) atomicAdd(a.tests, my_tests);
+    if (a.tests && lane == 0 && (n_tests | n_checks)) {
+        atomicAdd(a.tests, n_tests);
+        atomicAdd(a.tests + 1, n_checks);
+    }
 }
 
 template <int D, int SLOTS>
@@ -559,6 +606,7 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     a.cand = ws.cand;
     a.tmin = ws.tmin;
     a.magic = ws.magic;
+    a.steps = ws.steps;
     a.hdr = ws.hdr;
     a.res = ws.res;
     a.tests = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;

@@ -20,8 +20,8 @@ namespace gres {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;   // 4096 items per block
+constexpr int kItems = 4;
+constexpr int kTile = kThreads * kItems;   // 1024 items per block
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanThreads = 1024;
 

@@ -31,7 +31,6 @@ constexpr int kCT = 256;            // threads per compaction / filter block
 constexpr int kPer = 4;             // items per thread
 constexpr int kCB = kCT * kPer;     // items per compaction block
 constexpr int kTriThreads = 256;
-constexpr int kTriChunk = 1024;     // candidate rows staged per round
 
 template <int D>
 __device__ __forceinline__ void load_canon(const uint32_t *data, long long row, int dir, uint32_t (&x)[D]) {
@@ -153,34 +152,54 @@ __global__ void k_keys(const uint32_t *data, long long n, int dir, unsigned long
 }
 
 // Representatives: the first R rows in key order, minus those dominated by
-// another of them. One block of kMaxReps threads.
+// another of them. k_rep_flags: one warp per representative, lanes over the
+// other representatives (all R staged in shared memory by every block).
+constexpr int kRepBlock = 1024;
+template <int D>
+__global__ void __launch_bounds__(kRepBlock)
+k_rep_flags(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
+            int R, const WsHeader *h, uint32_t *rep_flag) {
+    __shared__ uint32_t rows[kMaxReps * D];
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    const int r_eff = (int)min((long long)R, n);
+    for (int i = threadIdx.x; i < r_eff; i += kRepBlock) {
+        uint32_t x[D];
+        load_canon<D>(data, vals[i], dir, x);
+        #pragma unroll
+        for (int q = 0; q < D; q++) rows[i * D + q] = x[q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kRepBlock / 32) + (threadIdx.x >> 5);
+    if (i >= r_eff) return;
+    uint32_t x[D];
+    #pragma unroll
+    for (int q = 0; q < D; q++) x[q] = rows[i * D + q];
+    bool dom = false;
+    for (int j0 = 0; j0 < r_eff && !dom; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        if (j < r_eff) {
+            uint32_t sv[D];
+            #pragma unroll
+            for (int q = 0; q < D; q++) sv[q] = rows[j * D + q];
+            hit = dominates<D>(sv, x);
+        }
+        dom = __any_sync(0xffffffffu, hit);
+    }
+    if (lane == 0) rep_flag[i] = dom ? 0u : 1u;
+}
+
+// Compacts the kept representatives (one block).
 template <int D>
 __global__ void __launch_bounds__(kMaxReps)
-k_reps(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
-       int R, uint32_t *reps, WsHeader *h) {
-    __shared__ uint32_t rows[kMaxReps * D];
+k_rep_compact(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
+              int R, const uint32_t *rep_flag, uint32_t *reps, WsHeader *h) {
     __shared__ uint32_t wsum[kMaxReps / 32];
     const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
     const int r_eff = (int)min((long long)R, n);
     const int i = threadIdx.x;
-    uint32_t x[D];
-    if (i < r_eff) {
-        load_canon<D>(data, vals[i], dir, x);
-        #pragma unroll
-        for (int j = 0; j < D; j++) rows[i * D + j] = x[j];
-    }
-    __syncthreads();
-    bool keep = false;
-    if (i < r_eff) {
-        keep = true;
-        for (int j = 0; j < r_eff && keep; j++) {
-            uint32_t s[D];
-            #pragma unroll
-            for (int q = 0; q < D; q++) s[q] = rows[j * D + q];
-            if (dominates<D>(s, x)) keep = false;
-        }
-    }
-    // block compaction of the kept representatives
+    const bool keep = i < r_eff && rep_flag[i] != 0u;
     const int lane = i & 31, w = i >> 5;
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) wsum[w] = __popc(bal);
@@ -191,19 +210,24 @@ k_reps(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *val
         all += wsum[j];
     }
     if (keep) {
-        const uint32_t pos = before + __popc(bal & ((1u << lane) - 1u));
-        store_row<D>(reps, pos, x);
+        uint32_t x[D];
+        load_canon<D>(data, vals[i], dir, x);
+        store_row<D>(reps, before + __popc(bal & ((1u << lane) - 1u)), x);
     }
     if (i == 0) h->n_reps = all;
 }
 
 // Survivor flags (not dominated by any representative) in key order, plus
-// per-block counts for the compaction.
+// per-block counts for the compaction. Each warp loads 32 rows (one per
+// lane), then takes them one at a time and tests the row against 32
+// representatives per iteration (lanes over representatives, stop at the first
+// dominating one).
 template <int D>
 __global__ void __launch_bounds__(kCT)
 k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
          const uint32_t *reps, const WsHeader *h, uint32_t *flags, uint32_t *blocksum) {
     __shared__ uint32_t rs[kMaxReps * D];
+    __shared__ uint32_t cnt;
     const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
     const int nr = (int)h->n_reps;
     for (int j = threadIdx.x; j < nr; j += kCT) {
@@ -212,28 +236,50 @@ k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *v
         #pragma unroll
         for (int q = 0; q < D; q++) rs[j * D + q] = x[q];
     }
+    if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    uint32_t cnt = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long b0 = (long long)blockIdx.x * kCB;
-    #pragma unroll 1
-    for (int r = 0; r < kPer; r++) {
-        const long long p = b0 + r * kCT + threadIdx.x;
-        if (p >= n) break;
+    uint32_t mine = 0;
+    for (int g = warp; g < kCB / 32; g += kCT / 32) {
+        const long long p = b0 + g * 32 + lane;
         uint32_t x[D];
-        load_canon<D>(data, vals[p], dir, x);
-        bool alive = true;
-        for (int j = 0; j < nr; j++) {
-            uint32_t s[D];
+        if (p < n) load_canon<D>(data, vals[p], dir, x);
+        else {
             #pragma unroll
-            for (int q = 0; q < D; q++) s[q] = rs[j * D + q];
-            if (dominates<D>(s, x)) { alive = false; break; }
+            for (int q = 0; q < D; q++) x[q] = 0u;
         }
-        flags[p] = alive ? 1u : 0u;
-        cnt += alive ? 1u : 0u;
+        unsigned alive_mask = 0;
+        const int lim = (int)min(32LL, n - (b0 + g * 32));
+        for (int l = 0; l < lim; l++) {
+            uint32_t xs[D];
+            #pragma unroll
+            for (int q = 0; q < D; q++) xs[q] = __shfl_sync(0xffffffffu, x[q], l);
+            bool dom = false;
+            for (int j0 = 0; j0 < nr && !dom; j0 += 32) {
+                const int j = j0 + lane;
+                bool hit = false;
+                if (j < nr) {
+                    uint32_t sv[D];
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) sv[q] = rs[j * D + q];
+                    hit = dominates<D>(sv, xs);
+                }
+                dom = __any_sync(0xffffffffu, hit);
+            }
+            if (!dom) alive_mask |= 1u << l;
+        }
+        if (p < n) {
+            const bool alive = (alive_mask >> lane) & 1u;
+            flags[p] = alive ? 1u : 0u;
+            mine += alive ? 1u : 0u;
+        }
     }
-    uint32_t tot;
-    block_scan(cnt, &tot);
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0 && mine) atomicAdd(&cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = cnt;
 }
 
 // Exclusive scan of blocksum[0 .. nb) in place (one block); *total = sum.
@@ -294,38 +340,34 @@ k_compact_surv(const uint32_t *data, int dir, const uint32_t *vals0, const uint3
 }
 
 // Final filter over survivors in key order: survivor q is a skyline tuple iff
-// no survivor j < q dominates it. Sets skyflag[original row].
+// no survivor j < q dominates it. One warp per survivor, lanes over 32 earlier
+// survivors per iteration (coalesced rows), stopping at the first dominator.
+// Warps take survivors from the last one down, so the longest scans start
+// first. Sets skyflag[original row].
 template <int D>
 __global__ void __launch_bounds__(kTriThreads)
 k_tri(const uint32_t *surv_rows, const uint32_t *surv_orig, const WsHeader *h, uint32_t *skyflag) {
-    constexpr int DP = padded_dims(D);
-    __shared__ __align__(16) uint32_t chunk[kTriChunk * DP];
     const long long M = h->n_surv;
-    const long long q0 = (long long)blockIdx.x * kTriThreads;
-    if (q0 >= M) return;
-    const long long q = q0 + threadIdx.x;
-    uint32_t x[D];
-    bool alive = q < M;
-    if (alive) load_row<D>(surv_rows, q, x);
-    const long long qmax = min(M, q0 + kTriThreads);   // candidates live in [0, qmax - 1)
-    for (long long c0 = 0; c0 < qmax - 1; c0 += kTriChunk) {
-        const int cnt = (int)min((long long)kTriChunk, qmax - 1 - c0);
-        const uint4 *src = reinterpret_cast<const uint4 *>(surv_rows + c0 * DP);
-        uint4 *dst = reinterpret_cast<uint4 *>(chunk);
-        for (int v = threadIdx.x; v < cnt * DP / 4; v += kTriThreads) dst[v] = src[v];
-        __syncthreads();
-        if (alive) {
-            const long long lim = q - c0;
-            const int jend = (int)min((long long)cnt, lim < 0 ? 0 : lim);
-            for (int j = 0; j < jend; j++) {
-                uint32_t s[D];
-                load_row<D>(chunk, j, s);
-                if (dominates<D>(s, x)) { alive = false; break; }
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * kTriThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * kTriThreads) >> 5;
+    for (long long r = wid; r < M; r += nw) {
+        const long long q = M - 1 - r;
+        uint32_t x[D];
+        load_row<D>(surv_rows, q, x);
+        bool dom = false;
+        for (long long c0 = 0; c0 < q && !dom; c0 += 32) {
+            const long long j = c0 + lane;
+            bool hit = false;
+            if (j < q) {
+                uint32_t sv[D];
+                load_row<D>(surv_rows, j, sv);
+                hit = dominates<D>(sv, x);
             }
+            dom = __any_sync(0xffffffffu, hit);
         }
-        if (!__syncthreads_or(alive)) break;
+        if (!dom && lane == 0) skyflag[surv_orig[q]] = 1u;
     }
-    if (q < M && alive) skyflag[surv_orig[q]] = 1u;
 }
 
 __global__ void __launch_bounds__(kCT)
@@ -373,7 +415,11 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     k_keys<D><<<kb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.vals[0], ws.hdr); note_launch();
     cudaError_t e = launch_radix_sort(ws, n, &ws.hdr->n_rows, 5, st);
     if (e != cudaSuccess) return e;
-    k_reps<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps, ws.reps, ws.hdr); note_launch();
+    const int r_eff = (int)std::min<int64_t>(reps, n);
+    k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps,
+                                                           ws.hdr, ws.perm); note_launch();
+    k_rep_compact<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps, ws.perm,
+                                            ws.reps, ws.hdr); note_launch();
     k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.reps, ws.hdr,
                                                ws.flags, ws.blocksum); note_launch();
     k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv); note_launch();
@@ -381,7 +427,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
                                                      ws.blocksum, ws.surv_rows, ws.surv_orig, ws.hdr); note_launch();
     e = cudaMemsetAsync(ws.flags, 0, sizeof(uint32_t) * (size_t)n, st);
     if (e != cudaSuccess) return e;
-    k_tri<D><<<(unsigned)((n + kTriThreads - 1) / kTriThreads), kTriThreads, 0, st>>>(
+    k_tri<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
         ws.surv_rows, ws.surv_orig, ws.hdr, ws.flags); note_launch();
     k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum); note_launch();
     k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky); note_launch();

@@ -180,12 +180,12 @@ def test_host_buffer_entry_and_counts():
     np.testing.assert_array_equal(hs, osky)
     np.testing.assert_array_equal(hr, ores)
     import torch
-    tests = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tests = torch.zeros(2, dtype=torch.int64, device="cuda")
     G.gres_compute(G.to_device_u32(data), steps, G.MIN, G.plan(G.PART_GRID, m=4, count_tests=True),
                    tests=tests)
-    executed = int(tests.item())
+    executed, checks = (int(v) for v in tests.cpu().tolist())
     S = len(osky)
-    assert 0 < executed <= S * 32 * S * 256
+    assert 0 < executed <= S * 32 * S * 256 and checks > 0
 
 
 def test_sky_compute_only():
