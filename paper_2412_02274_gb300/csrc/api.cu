@@ -179,11 +179,15 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.vals[0] = static_cast<uint32_t *>(take(4 * nn));
     w.vals[1] = static_cast<uint32_t *>(take(4 * nn));
     w.hist = static_cast<uint32_t *>(take(4 * 256 * (sort_blocks(nn) + 1)));
+    w.dtot = static_cast<uint32_t *>(take(4 * 256));
     w.blocksum = static_cast<uint32_t *>(take(4 * (scan_blocks(nn) + 1)));
     w.flags = static_cast<uint32_t *>(take(4 * nn));
     w.surv_rows = static_cast<uint32_t *>(take(4 * DP * nn));
     w.surv_orig = static_cast<uint32_t *>(take(4 * nn));
     w.reps = static_cast<uint32_t *>(take(4 * DP * kMaxReps));
+    w.sel_hist = static_cast<uint32_t *>(take(4 * 2 * 4096));
+    w.rep_key = static_cast<unsigned long long *>(take(8 * kMaxReps));
+    w.rep_idx = static_cast<uint32_t *>(take(4 * kMaxReps));
     w.sky_rows = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.cand = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.tmin = static_cast<uint32_t *>(take(4 * DP * tiles));

@@ -35,12 +35,16 @@ struct WsHeader {
     long long n_surv;             // rows left after the representative filter
     long long n_sky;              // skyline size S
     long long n_reps;             // representatives kept (mutually non-dominated)
+    long long n_cand;             // representative candidates (smallest keys)
+    unsigned long long sel_thr;   // selection threshold on (f - f_min) >> sh2
+    unsigned int sel_b1;          // level-1 selection bucket
+    unsigned int sel_below;       // rows under bucket sel_b1
     unsigned int work_next;       // dynamic work counter of the gres kernel
     unsigned int status;          // kStatus* bits
     unsigned int sorted_sel;      // buffer (0/1) holding the last radix sort's result
     unsigned int lo[kMaxD];       // per-attribute canonical minimum over the skyline
     unsigned int hi[kMaxD];       // per-attribute canonical maximum over the skyline
-    unsigned int pad[11];
+    unsigned int pad[5];
 };
 
 // Digit passes that do work in the radix sort of the current key range; the
@@ -57,11 +61,15 @@ struct Workspace {
     unsigned long long *keys[2];  // radix sort key ping-pong, n each
     uint32_t *vals[2];            // radix sort value ping-pong, n each
     uint32_t *hist;               // 256 * sort_blocks(n)
+    uint32_t *dtot;               // 256 digit totals of the current pass
     uint32_t *blocksum;           // compaction block sums
     uint32_t *flags;              // n
     uint32_t *surv_rows;          // n * DP canonical rows, sum order
     uint32_t *surv_orig;          // n original row numbers, sum order
     uint32_t *reps;               // kMaxReps * DP
+    uint32_t *sel_hist;           // 2 * 4096 selection histogram counters
+    unsigned long long *rep_key;  // kMaxReps representative candidate keys
+    uint32_t *rep_idx;            // kMaxReps representative candidate rows
     uint32_t *sky_rows;           // (n + tile) * DP canonical rows, skyline order
     uint32_t *cand;               // (n + tile) * DP canonical rows, partition order
     uint32_t *tmin;               // tiles * DP per-tile minima

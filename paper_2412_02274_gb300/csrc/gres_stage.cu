@@ -117,6 +117,9 @@ __global__ void k_sky_range(const uint32_t *sky_rows, WsHeader *h) {
         #pragma unroll
         for (int i = 0; i < D; i++) { lo[i] = min(lo[i], x[i]); hi[i] = max(hi[i], x[i]); }
     }
+    __shared__ uint32_t blo[D], bhi[D];
+    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
+    __syncthreads();
     #pragma unroll
     for (int i = 0; i < D; i++) {
         #pragma unroll
@@ -125,9 +128,14 @@ __global__ void k_sky_range(const uint32_t *sky_rows, WsHeader *h) {
             hi[i] = max(hi[i], __shfl_xor_sync(kFull, hi[i], o));
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicMin(&h->lo[i], lo[i]);
-            atomicMax(&h->hi[i], hi[i]);
+            atomicMin(&blo[i], lo[i]);
+            atomicMax(&bhi[i], hi[i]);
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        atomicMin(&h->lo[threadIdx.x], blo[threadIdx.x]);
+        atomicMax(&h->hi[threadIdx.x], bhi[threadIdx.x]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         h->key_min = ~0ull;
@@ -568,7 +576,7 @@ cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
 template <int D, int SLOTS>
 cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Workspace &ws,
                           int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
-    const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count * 4);
+    const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count);
     stage_begin(kStagePartition, st);
     k_sky_range<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr); note_launch();
     const int scheme = cfg.scheme;
@@ -586,15 +594,22 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
             pa.thr[j] = (unsigned long long)std::llround(t * t * 4294967296.0);
         }
     }
+    // key widths are known on the host: partition number << 16 | 16-bit order
+    auto bits_of = [](unsigned long long v) { int b = 0; while (v) { b++; v >>= 1; } return b; };
+    auto passes = [&](int bits) { return (bits + 7) / 8; };
+    unsigned long long cells = 1;
+    if (scheme == GRES_PART_GRID || scheme == GRES_PART_ANGULAR)
+        for (int i = 0; i < (scheme == GRES_PART_GRID ? D : D - 1); i++) cells *= (unsigned long long)cfg.m;
     cudaError_t e;
     if (scheme != GRES_PART_NONE) {
         k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]); note_launch();
-        e = launch_radix_sort(ws, n, &ws.hdr->n_sky, 8, st);
+        const int bits1 = scheme == GRES_PART_SLICED ? 32 : 16 + bits_of(cells - 1);
+        e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(bits1), st);
         if (e != cudaSuccess) return e;
         if (scheme == GRES_PART_SLICED) {
             k_reset_keyrange<<<1, 1, 0, st>>>(ws.hdr); note_launch();
             k_sliced_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0], ws.vals[1]); note_launch();
-            e = launch_radix_sort(ws, n, &ws.hdr->n_sky, 8, st);
+            e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(16 + bits_of((unsigned long long)cfg.p - 1)), st);
             if (e != cudaSuccess) return e;
         }
     }

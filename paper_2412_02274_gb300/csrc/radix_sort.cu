@@ -8,11 +8,12 @@
 // which a last one-thread kernel records in hdr->sorted_sel. Digits are
 // taken from key - key_min.
 //
-// Each pass is three kernels: per-block digit histograms, one exclusive scan
-// over the (digit-major, block-minor) histogram table, and a stable scatter
-// in which each block ranks its items per digit in input order (warp
-// match_any for ranks within a warp, a per-digit prefix over warps for the
-// block, a running per-digit carry across the block's rounds).
+// Each pass is three kernels: per-block digit histograms, a per-digit scan
+// over the blocks (one block per digit, with the digit totals), and a stable
+// scatter in which each block takes its digit offsets from the totals and
+// ranks its items per digit in input order (warp match_any for ranks within a
+// warp, a per-digit prefix over warps for the block, a running per-digit carry
+// across the block's rounds).
 #include "gres_internal.cuh"
 
 namespace gres {
@@ -23,7 +24,6 @@ constexpr int kThreads = 256;
 constexpr int kItems = 4;
 constexpr int kTile = kThreads * kItems;   // 1024 items per block
 constexpr int kWarps = kThreads / 32;
-constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kThreads)
 k_hist(WsHeader *h, const unsigned long long *keys_in, uint32_t *hist, const long long *d_n, int pass) {
@@ -46,51 +46,46 @@ k_hist(WsHeader *h, const unsigned long long *keys_in, uint32_t *hist, const lon
     hist[(long long)threadIdx.x * G + blockIdx.x] = sh[threadIdx.x];
 }
 
-// Exclusive scan of hist[0 .. 256*G) in place (one block).
+// Per-digit exclusive scan over the blocks: block d scans hist[d*G .. d*G+G)
+// in place and writes the digit's total to dtot[d].
+constexpr int kScanThreads = 256;
 __global__ void __launch_bounds__(kScanThreads)
-k_scan(WsHeader *h, uint32_t *hist, const long long *d_n, int pass) {
+k_scan(WsHeader *h, uint32_t *hist, uint32_t *dtot, const long long *d_n, int pass) {
     if (pass >= radix_passes(h)) return;
     const long long n = *d_n;
     const long long G = (n + kTile - 1) / kTile;
-    const long long total = 256 * G;
-    if (total == 0) return;
-    const long long chunk = (total + kScanThreads - 1) / kScanThreads;
-    const long long c0 = (long long)threadIdx.x * chunk;
-    const long long c1 = min(c0 + chunk, total);
-    uint32_t local = 0;
-    for (long long i = c0; i < c1; i++) local += hist[i];
-    // block exclusive scan of `local`
+    uint32_t *row = hist + (long long)blockIdx.x * G;
     __shared__ uint32_t warp_tot[kScanThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t incl = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        uint32_t v = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
-        uint32_t vi = v;
+    uint32_t carry = 0;
+    for (long long c0 = 0; c0 < G; c0 += kScanThreads) {
+        const long long i = c0 + threadIdx.x;
+        const uint32_t v = i < G ? row[i] : 0u;
+        uint32_t incl = v;
+        #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
-            if (lane >= o) vi += y;
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        if (lane < kScanThreads / 32) warp_tot[lane] = vi - v;
+        if (lane == 31) warp_tot[w] = incl;
+        __syncthreads();
+        uint32_t before = 0, all = 0;
+        #pragma unroll
+        for (int j = 0; j < kScanThreads / 32; j++) {
+            before += j < w ? warp_tot[j] : 0u;
+            all += warp_tot[j];
+        }
+        if (i < G) row[i] = carry + before + incl - v;
+        carry += all;
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = warp_tot[w] + incl - local;
-    for (long long i = c0; i < c1; i++) {
-        uint32_t c = hist[i];
-        hist[i] = run;
-        run += c;
-    }
+    if (threadIdx.x == 0) dtot[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_in,
           unsigned long long *keys_out, uint32_t *vals_out, const uint32_t *hist,
-          const long long *d_n, int pass) {
+          const uint32_t *dtot, const long long *d_n, int pass) {
     if (pass >= radix_passes(h)) return;
     const long long n = *d_n;
     const long long G = (n + kTile - 1) / kTile;
@@ -98,8 +93,24 @@ k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_i
     __shared__ uint32_t base[256];
     __shared__ uint32_t wcnt[kWarps][256];
     __shared__ uint32_t woff[kWarps][256];
+    __shared__ uint32_t wsum[kWarps];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    base[tid] = hist[(long long)tid * G + blockIdx.x];
+    {
+        // digit offsets: exclusive scan of the 256 digit totals
+        const uint32_t v = dtot[tid];
+        uint32_t incl = v;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        #pragma unroll
+        for (int j = 0; j < kWarps; j++) before += j < w ? wsum[j] : 0u;
+        base[tid] = before + incl - v + hist[(long long)tid * G + blockIdx.x];
+    }
     for (int j = 0; j < kWarps; j++) wcnt[j][tid] = 0;
     __syncthreads();
     const unsigned long long kmin = h->key_min;
@@ -161,9 +172,9 @@ cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n
     for (int p = 0; p < max_passes; p++) {
         const int in = p & 1, out = (p + 1) & 1;
         k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p); note_launch();
-        k_scan<<<1, kScanThreads, 0, st>>>(ws.hdr, ws.hist, d_n, p); note_launch();
+        k_scan<<<256, kScanThreads, 0, st>>>(ws.hdr, ws.hist, ws.dtot, d_n, p); note_launch();
         k_scatter<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.vals[in], ws.keys[out],
-                                                    ws.vals[out], ws.hist, d_n, p); note_launch();
+                                                    ws.vals[out], ws.hist, ws.dtot, d_n, p); note_launch();
     }
     k_sort_done<<<1, 1, 0, st>>>(ws.hdr); note_launch();
     return cudaGetLastError();

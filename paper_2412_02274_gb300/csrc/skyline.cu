@@ -1,23 +1,23 @@
 // skyline.cu -- Sky(r) (Def. 1) by a sort-by-sum pass with block dominance filters.
 //
 // Pipeline (all sizes after n live in the workspace header):
-//   1. keys:   canonical rows (smaller is better; GRES_MAX reads ~v) and the
-//              key f(t) = sum of the canonical values. f is monotone, so
-//              s dominates t implies f(s) < f(t): in ascending key order a
-//              tuple can only be dominated by an earlier one (the ordering
-//              of sort-filter-skyline, cited in Sec. 4).
-//   2. sort:   stable radix sort of (key, row) -- ties keep row order.
-//   3. reps:   the first R rows of the order; those dominated by another of
-//              them are dropped (Representative Filtering, Sec. 3.1). The
-//              rest are skyline tuples: only earlier, smaller-key rows could
-//              dominate them and those are all representatives.
-//   4. filter: every row is tested against the representatives.
-//   5. compact the survivors, in key order.
-//   6. final:  each survivor is tested against every EARLIER survivor; it is
-//              in the skyline iff none dominates it. (If t is dominated, a
-//              skyline tuple with a smaller key dominates it, and skyline
-//              tuples always survive step 4.)
-//   7. flags by original row -> ascending row numbers, plus the canonical
+//   1. keys:    canonical rows (smaller is better; GRES_MAX reads ~v) and the
+//               key f(t) = sum of the canonical values. f is monotone, so s
+//               dominates t implies f(s) < f(t).
+//   2. select:  the representatives of Representative Filtering (Sec. 3.1):
+//               the rows with the smallest f, found by a selection (two
+//               12-bit histogram rounds over f give a threshold leaving at
+//               most R rows below it), then sorted by (f, row). Those
+//               dominated by another representative are dropped.
+//   3. filter:  every row, in input order, against the representatives.
+//   4. sort:    the survivors by (f, row) -- the sort-filter-skyline order
+//               (cited in Sec. 4): a survivor can only be dominated by an
+//               earlier one.
+//   5. final:   each survivor against every EARLIER survivor; it is in the
+//               skyline iff none dominates it. (If t is dominated, a skyline
+//               tuple with a smaller f dominates it, and skyline tuples
+//               always survive step 3.)
+//   6. flags by original row -> ascending row numbers, plus the canonical
 //      skyline rows for the gres stage.
 #include "gres_internal.cuh"
 
@@ -28,7 +28,7 @@ namespace gres {
 namespace {
 
 constexpr int kCT = 256;            // threads per compaction / filter block
-constexpr int kPer = 4;             // items per thread
+constexpr int kPer = 2;             // items per thread
 constexpr int kCB = kCT * kPer;     // items per compaction block
 constexpr int kTriThreads = 256;
 
@@ -112,6 +112,7 @@ __global__ void k_init(WsHeader *h, long long n) {
         h->n_surv = 0;
         h->n_sky = 0;
         h->n_reps = 0;
+        h->n_cand = 0;
         h->work_next = 0;
         h->status = 0;
         h->sorted_sel = 0;
@@ -122,22 +123,8 @@ __global__ void k_init(WsHeader *h, long long n) {
     }
 }
 
-template <int D>
-__global__ void k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys,
-                       uint32_t *vals, WsHeader *h) {
-    unsigned long long kmin = ~0ull, kmax = 0ull;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        uint32_t x[D];
-        load_canon<D>(data, i, dir, x);
-        unsigned long long k = 0;
-        #pragma unroll
-        for (int j = 0; j < D; j++) k += x[j];
-        keys[i] = k;
-        vals[i] = (uint32_t)i;
-        kmin = k < kmin ? k : kmin;
-        kmax = k > kmax ? k : kmax;
-    }
+__device__ __forceinline__ void warp_minmax_atomic(unsigned long long kmin, unsigned long long kmax,
+                                                   WsHeader *h) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, o);
@@ -151,38 +138,190 @@ __global__ void k_keys(const uint32_t *data, long long n, int dir, unsigned long
     }
 }
 
-// Representatives: the first R rows in key order, minus those dominated by
-// another of them. k_rep_flags: one warp per representative, lanes over the
-// other representatives (all R staged in shared memory by every block).
+template <int D>
+__global__ void k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys, WsHeader *h) {
+    unsigned long long kmin = ~0ull, kmax = 0ull;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        uint32_t x[D];
+        load_canon<D>(data, i, dir, x);
+        unsigned long long k = 0;
+        #pragma unroll
+        for (int j = 0; j < D; j++) k += x[j];
+        keys[i] = k;
+        kmin = k < kmin ? k : kmin;
+        kmax = k > kmax ? k : kmax;
+    }
+    warp_minmax_atomic(kmin, kmax, h);
+}
+
+// ---- representative selection ------------------------------------------------
+// Level 1 buckets f - f_min by its top 12 bits (shift sh1); level 2 splits the
+// bucket where the count passes R by the next (up to 12) bits (shift sh2).
+constexpr int kSelBuckets = 4096;
+
+__device__ __forceinline__ int sel_shift1(const WsHeader *h) {
+    const unsigned long long range = h->key_max >= h->key_min ? h->key_max - h->key_min : 0ull;
+    const int bits = range ? 64 - __clzll((long long)range) : 0;
+    return bits > 12 ? bits - 12 : 0;
+}
+
+__global__ void k_sel_hist(const unsigned long long *keys, long long n, const WsHeader *h, int level,
+                           uint32_t *hist) {
+    __shared__ uint32_t sh[kSelBuckets];
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    const unsigned long long kmin = h->key_min;
+    const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
+    const unsigned long long b1 = h->sel_b1;
+    const bool active = level == 1 || b1 < kSelBuckets;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; active && i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long kn = keys[i] - kmin;
+        if (level == 1) {
+            atomicAdd(&sh[kn >> sh1], 1u);
+        } else if ((kn >> sh1) == b1) {
+            atomicAdd(&sh[(kn >> sh2) & ((1ull << (sh1 - sh2)) - 1ull)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+}
+
+// One block of 1024 threads: first bucket at which the running count (plus
+// `below` for level 2) exceeds R. Level 1 writes sel_b1 and sel_below (the
+// count under bucket b1; sel_b1 = 4096 when every row fits); level 2 writes
+// the final threshold sel_thr in units of 2^sh2 (rows with
+// (f - f_min) >> sh2 < sel_thr are representatives: at most R of them).
+__global__ void __launch_bounds__(1024) k_sel_find(const uint32_t *hist, int level, int R, WsHeader *h) {
+    __shared__ uint32_t wsum[32];
+    __shared__ unsigned long long found;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (level == 2 && h->sel_b1 >= (unsigned)kSelBuckets) {
+        if (tid == 0) h->sel_thr = ~0ull;
+        return;
+    }
+    if (tid == 0) found = ~0ull;
+    const uint32_t base = level == 1 ? 0u : h->sel_below;
+    uint32_t c[4], local = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; q++) { c[q] = hist[4 * tid + q]; local += c[q]; }
+    uint32_t incl = local;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int j = 0; j < 32; j++) before += j < w ? wsum[j] : 0u;
+    uint32_t run = base + before + incl - local;
+    #pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (run + c[q] > (uint32_t)R) {
+            atomicMin(&found, ((unsigned long long)(4 * tid + q) << 32) | run);
+            break;
+        }
+        run += c[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
+        if (level == 1) {
+            if (found == ~0ull) { h->sel_b1 = kSelBuckets; h->sel_below = 0; }
+            else { h->sel_b1 = (uint32_t)(found >> 32); h->sel_below = (uint32_t)found; }
+        } else {
+            const unsigned long long b2 = found == ~0ull ? (1ull << (sh1 - sh2)) : (found >> 32);
+            h->sel_thr = ((unsigned long long)h->sel_b1 << (sh1 - sh2)) + b2;
+        }
+    }
+}
+
+// Rows under the threshold, appended in any order (sorted next).
+__global__ void k_sel_gather(const unsigned long long *keys, long long n, WsHeader *h,
+                             unsigned long long *rep_key, uint32_t *rep_idx) {
+    const unsigned long long kmin = h->key_min, thr = h->sel_thr;
+    const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long kn = keys[i] - kmin;
+        if ((kn >> sh2) < thr) {
+            const unsigned pos = atomicAdd(reinterpret_cast<unsigned *>(&h->n_cand), 1u);
+            if (pos < (unsigned)kMaxReps) {
+                rep_key[pos] = keys[i];
+                rep_idx[pos] = (uint32_t)i;
+            }
+        }
+    }
+}
+
+// Sorts the candidates by (f, row) (bitonic, one block) and writes their
+// canonical rows to `rows` in that order.
+template <int D>
+__global__ void __launch_bounds__(kMaxReps)
+k_rep_sort(const uint32_t *data, int dir, const unsigned long long *rep_key, const uint32_t *rep_idx,
+           WsHeader *h, uint32_t *rows) {
+    __shared__ unsigned long long sk[kMaxReps];
+    __shared__ uint32_t si[kMaxReps];
+    const int tid = threadIdx.x;
+    const int nc = (int)min((long long)h->n_cand, (long long)kMaxReps);
+    sk[tid] = tid < nc ? rep_key[tid] : ~0ull;
+    si[tid] = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int size = 2; size <= kMaxReps; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int j = tid ^ stride;
+            if (j > tid) {
+                const bool asc = (tid & size) == 0;
+                const bool gt = sk[tid] > sk[j] || (sk[tid] == sk[j] && si[tid] > si[j]);
+                if (gt == asc) {
+                    unsigned long long tk = sk[tid]; sk[tid] = sk[j]; sk[j] = tk;
+                    uint32_t ti = si[tid]; si[tid] = si[j]; si[j] = ti;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid < nc) {
+        uint32_t x[D];
+        load_canon<D>(data, si[tid], dir, x);
+        store_row<D>(rows, tid, x);
+    }
+    if (tid == 0) h->n_cand = nc;
+}
+
+// Representatives dominated by another one are dropped (Sec. 3.1). One warp
+// per candidate, lanes over the other candidates (all staged in shared
+// memory by every block).
 constexpr int kRepBlock = 1024;
 template <int D>
 __global__ void __launch_bounds__(kRepBlock)
-k_rep_flags(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
-            int R, const WsHeader *h, uint32_t *rep_flag) {
-    __shared__ uint32_t rows[kMaxReps * D];
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    const int r_eff = (int)min((long long)R, n);
-    for (int i = threadIdx.x; i < r_eff; i += kRepBlock) {
+k_rep_flags(const uint32_t *cand_rows, const WsHeader *h, uint32_t *rep_flag) {
+    __shared__ uint32_t rows[D * kMaxReps];
+    const int nc = (int)h->n_cand;
+    for (int i = threadIdx.x; i < nc; i += kRepBlock) {
         uint32_t x[D];
-        load_canon<D>(data, vals[i], dir, x);
+        load_row<D>(cand_rows, i, x);
         #pragma unroll
-        for (int q = 0; q < D; q++) rows[i * D + q] = x[q];
+        for (int q = 0; q < D; q++) rows[q * kMaxReps + i] = x[q];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (kRepBlock / 32) + (threadIdx.x >> 5);
-    if (i >= r_eff) return;
+    if (i >= nc) return;
     uint32_t x[D];
     #pragma unroll
-    for (int q = 0; q < D; q++) x[q] = rows[i * D + q];
+    for (int q = 0; q < D; q++) x[q] = rows[q * kMaxReps + i];
     bool dom = false;
-    for (int j0 = 0; j0 < r_eff && !dom; j0 += 32) {
+    for (int j0 = 0; j0 < nc && !dom; j0 += 32) {
         const int j = j0 + lane;
         bool hit = false;
-        if (j < r_eff) {
+        if (j < nc) {
             uint32_t sv[D];
             #pragma unroll
-            for (int q = 0; q < D; q++) sv[q] = rows[j * D + q];
+            for (int q = 0; q < D; q++) sv[q] = rows[q * kMaxReps + j];
             hit = dominates<D>(sv, x);
         }
         dom = __any_sync(0xffffffffu, hit);
@@ -190,16 +329,16 @@ k_rep_flags(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t
     if (lane == 0) rep_flag[i] = dom ? 0u : 1u;
 }
 
-// Compacts the kept representatives (one block).
+// Keeps the non-dominated candidates, in order, in place (one block).
 template <int D>
 __global__ void __launch_bounds__(kMaxReps)
-k_rep_compact(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
-              int R, const uint32_t *rep_flag, uint32_t *reps, WsHeader *h) {
+k_rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
     __shared__ uint32_t wsum[kMaxReps / 32];
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    const int r_eff = (int)min((long long)R, n);
     const int i = threadIdx.x;
-    const bool keep = i < r_eff && rep_flag[i] != 0u;
+    const int nc = (int)h->n_cand;
+    const bool keep = i < nc && rep_flag[i] != 0u;
+    uint32_t x[D];
+    if (keep) load_row<D>(rows, i, x);
     const int lane = i & 31, w = i >> 5;
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) wsum[w] = __popc(bal);
@@ -209,32 +348,27 @@ k_rep_compact(const uint32_t *data, int dir, const uint32_t *vals0, const uint32
         before += j < w ? wsum[j] : 0u;
         all += wsum[j];
     }
-    if (keep) {
-        uint32_t x[D];
-        load_canon<D>(data, vals[i], dir, x);
-        store_row<D>(reps, before + __popc(bal & ((1u << lane) - 1u)), x);
-    }
+    if (keep) store_row<D>(rows, before + __popc(bal & ((1u << lane) - 1u)), x);
     if (i == 0) h->n_reps = all;
 }
 
-// Survivor flags (not dominated by any representative) in key order, plus
-// per-block counts for the compaction. Each warp loads 32 rows (one per
+// Survivor flags (not dominated by any representative), rows in input order,
+// plus per-block counts for the compaction. Each warp loads 32 rows (one per
 // lane), then takes them one at a time and tests the row against 32
-// representatives per iteration (lanes over representatives, stop at the first
-// dominating one).
+// representatives per iteration (lanes over representatives, stopping at the
+// first dominating one).
 template <int D>
 __global__ void __launch_bounds__(kCT)
-k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1, long long n,
-         const uint32_t *reps, const WsHeader *h, uint32_t *flags, uint32_t *blocksum) {
-    __shared__ uint32_t rs[kMaxReps * D];
+k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, const WsHeader *h,
+         uint32_t *flags, uint32_t *blocksum) {
+    __shared__ uint32_t rs[D * kMaxReps];   // attribute-major: lane j reads word j (no conflicts)
     __shared__ uint32_t cnt;
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
     const int nr = (int)h->n_reps;
     for (int j = threadIdx.x; j < nr; j += kCT) {
         uint32_t x[D];
         load_row<D>(reps, j, x);
         #pragma unroll
-        for (int q = 0; q < D; q++) rs[j * D + q] = x[q];
+        for (int q = 0; q < D; q++) rs[q * kMaxReps + j] = x[q];
     }
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -244,7 +378,7 @@ k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *v
     for (int g = warp; g < kCB / 32; g += kCT / 32) {
         const long long p = b0 + g * 32 + lane;
         uint32_t x[D];
-        if (p < n) load_canon<D>(data, vals[p], dir, x);
+        if (p < n) load_canon<D>(data, p, dir, x);
         else {
             #pragma unroll
             for (int q = 0; q < D; q++) x[q] = 0u;
@@ -262,7 +396,7 @@ k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *v
                 if (j < nr) {
                     uint32_t sv[D];
                     #pragma unroll
-                    for (int q = 0; q < D; q++) sv[q] = rs[j * D + q];
+                    for (int q = 0; q < D; q++) sv[q] = rs[q * kMaxReps + j];
                     hit = dominates<D>(sv, xs);
                 }
                 dom = __any_sync(0xffffffffu, hit);
@@ -283,8 +417,9 @@ k_filter(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *v
 }
 
 // Exclusive scan of blocksum[0 .. nb) in place (one block); *total = sum.
+// With reset_keys the sort-key range is cleared for the next key pass.
 __global__ void __launch_bounds__(1024)
-k_scan_blocks(uint32_t *blocksum, long long nb, long long *total) {
+k_scan_blocks(uint32_t *blocksum, long long nb, long long *total, WsHeader *h, int reset_keys) {
     __shared__ uint32_t wsum[32];
     const long long chunk = (nb + 1023) / 1024;
     const long long c0 = (long long)threadIdx.x * chunk;
@@ -310,18 +445,22 @@ k_scan_blocks(uint32_t *blocksum, long long nb, long long *total) {
         blocksum[i] = run;
         run += c;
     }
-    if (threadIdx.x == 0) *total = all;
+    if (threadIdx.x == 0) {
+        *total = all;
+        if (reset_keys) { h->key_min = ~0ull; h->key_max = 0ull; }
+    }
 }
 
-// Survivors, in key order: canonical rows and original row numbers.
+// Survivors in input order: canonical rows, original row numbers, and the
+// (f, position) pairs for the survivor sort (f recomputed from the row).
 template <int D>
 __global__ void __launch_bounds__(kCT)
-k_compact_surv(const uint32_t *data, int dir, const uint32_t *vals0, const uint32_t *vals1,
-               long long n, const uint32_t *flags, const uint32_t *blocksum, uint32_t *surv_rows,
-               uint32_t *surv_orig, const WsHeader *h) {
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+k_compact_surv(const uint32_t *data, int dir, long long n, const uint32_t *flags, const uint32_t *blocksum,
+               uint32_t *surv_rows, uint32_t *surv_orig, unsigned long long *keys, uint32_t *vals,
+               WsHeader *h) {
     uint32_t run = blocksum[blockIdx.x];
     const long long b0 = (long long)blockIdx.x * kCB;
+    unsigned long long kmin = ~0ull, kmax = 0ull;
     #pragma unroll 1
     for (int r = 0; r < kPer; r++) {
         const long long p = b0 + r * kCT + threadIdx.x;
@@ -329,19 +468,47 @@ k_compact_surv(const uint32_t *data, int dir, const uint32_t *vals0, const uint3
         uint32_t tot;
         const uint32_t ex = block_scan(f, &tot);
         if (f) {
-            const uint32_t row = vals[p];
             uint32_t x[D];
-            load_canon<D>(data, row, dir, x);
+            load_canon<D>(data, p, dir, x);
             store_row<D>(surv_rows, run + ex, x);
-            surv_orig[run + ex] = row;
+            surv_orig[run + ex] = (uint32_t)p;
+            unsigned long long k = 0;
+            #pragma unroll
+            for (int q = 0; q < D; q++) k += x[q];
+            keys[run + ex] = k;
+            vals[run + ex] = run + ex;
+            kmin = k < kmin ? k : kmin;
+            kmax = k > kmax ? k : kmax;
         }
         run += tot;
+    }
+    warp_minmax_atomic(kmin, kmax, h);
+}
+
+// Survivors in sorted order: rows into `out_rows`, original row numbers into
+// `out_orig`.
+template <int D>
+__global__ void k_gather_sorted(const uint32_t *surv_rows, const uint32_t *surv_orig, const uint32_t *vals0,
+                                const uint32_t *vals1, const WsHeader *h, uint32_t *out_rows,
+                                uint32_t *out_orig) {
+    constexpr int DP = padded_dims(D);
+    const long long M = h->n_surv;
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < M;
+         r += (long long)gridDim.x * blockDim.x) {
+        const uint32_t j = vals[r];
+        const uint4 *src = reinterpret_cast<const uint4 *>(surv_rows + (long long)j * DP);
+        uint4 *dst = reinterpret_cast<uint4 *>(out_rows + r * DP);
+        dst[0] = src[0];
+        if (DP == 8) dst[1] = src[1];
+        out_orig[r] = surv_orig[j];
     }
 }
 
 // Final filter over survivors in key order: survivor q is a skyline tuple iff
-// no survivor j < q dominates it. One warp per survivor, lanes over 32 earlier
-// survivors per iteration (coalesced rows), stopping at the first dominator.
+// no survivor j < q dominates it. One warp per survivor, lanes over 128 earlier
+// survivors per iteration (4 coalesced rows per lane), stopping at the first
+// dominator.
 // Warps take survivors from the last one down, so the longest scans start
 // first. Sets skyflag[original row].
 template <int D>
@@ -356,13 +523,18 @@ k_tri(const uint32_t *surv_rows, const uint32_t *surv_orig, const WsHeader *h, u
         uint32_t x[D];
         load_row<D>(surv_rows, q, x);
         bool dom = false;
-        for (long long c0 = 0; c0 < q && !dom; c0 += 32) {
-            const long long j = c0 + lane;
+        for (long long c0 = 0; c0 < q && !dom; c0 += 128) {
+            uint32_t sv[4][D];
+            #pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const long long j = c0 + 32 * u + lane;
+                if (j < q) load_row<D>(surv_rows, j, sv[u]);
+            }
             bool hit = false;
-            if (j < q) {
-                uint32_t sv[D];
-                load_row<D>(surv_rows, j, sv);
-                hit = dominates<D>(sv, x);
+            #pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const long long j = c0 + 32 * u + lane;
+                hit |= j < q && dominates<D>(sv[u], x);
             }
             dom = __any_sync(0xffffffffu, hit);
         }
@@ -411,26 +583,34 @@ template <int D>
 cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Workspace &ws,
                       int64_t *d_sky_idx, cudaStream_t st) {
     const long long nb = (n + kCB - 1) / kCB;
-    const int kb = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
-    k_keys<D><<<kb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.vals[0], ws.hdr); note_launch();
-    cudaError_t e = launch_radix_sort(ws, n, &ws.hdr->n_rows, 5, st);
+    const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 4);
+    k_keys<D><<<gb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.hdr); note_launch();
+    cudaError_t e = cudaMemsetAsync(ws.sel_hist, 0, sizeof(uint32_t) * 2 * kSelBuckets, st);
     if (e != cudaSuccess) return e;
+    const int hb = (int)std::min<long long>((n + 1023) / 1024, 152LL * 2);
+    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 1, ws.sel_hist); note_launch();
+    k_sel_find<<<1, 1024, 0, st>>>(ws.sel_hist, 1, reps, ws.hdr); note_launch();
+    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 2, ws.sel_hist + kSelBuckets); note_launch();
+    k_sel_find<<<1, 1024, 0, st>>>(ws.sel_hist + kSelBuckets, 2, reps, ws.hdr); note_launch();
+    k_sel_gather<<<gb, 256, 0, st>>>(ws.keys[0], n, ws.hdr, ws.rep_key, ws.rep_idx); note_launch();
+    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps); note_launch();
     const int r_eff = (int)std::min<int64_t>(reps, n);
-    k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps,
-                                                           ws.hdr, ws.perm); note_launch();
-    k_rep_compact<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, reps, ws.perm,
-                                            ws.reps, ws.hdr); note_launch();
-    k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.reps, ws.hdr,
-                                               ws.flags, ws.blocksum); note_launch();
-    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv); note_launch();
-    k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, ws.vals[0], ws.vals[1], n, ws.flags,
-                                                     ws.blocksum, ws.surv_rows, ws.surv_orig, ws.hdr); note_launch();
+    k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(ws.reps, ws.hdr, ws.perm); note_launch();
+    k_rep_compact<D><<<1, kMaxReps, 0, st>>>(ws.reps, ws.perm, ws.hdr); note_launch();
+    k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum); note_launch();
+    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv, ws.hdr, 1); note_launch();
+    k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
+                                                     ws.surv_orig, ws.keys[0], ws.vals[0], ws.hdr); note_launch();
+    e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 5, st);
+    if (e != cudaSuccess) return e;
+    k_gather_sorted<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1], ws.hdr,
+                                           ws.cand, ws.perm); note_launch();
     e = cudaMemsetAsync(ws.flags, 0, sizeof(uint32_t) * (size_t)n, st);
     if (e != cudaSuccess) return e;
     k_tri<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
-        ws.surv_rows, ws.surv_orig, ws.hdr, ws.flags); note_launch();
+        ws.cand, ws.perm, ws.hdr, ws.flags); note_launch();
     k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum); note_launch();
-    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky); note_launch();
+    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky, ws.hdr, 0); note_launch();
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
                                                     ws.sky_rows); note_launch();
     return cudaGetLastError();
