@@ -354,18 +354,8 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 template <int D>
 __host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 ? 384 : 256); }
 
-constexpr int kTileKeys = 8;                 // tile keys per lane in one selection round
+constexpr int kTileKeys = 8;                 // tile keys per lane in one selection round (<= 256 tiles)
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
-
-// First index in ws[0 .. n) whose width exceeds e (ws ascending).
-__device__ __forceinline__ int first_wider(const uint32_t *ws, int n, uint32_t e) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (ws[mid] <= e) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
 template <int D, int SLOTS, bool RES>
 __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *cand, const uint32_t *tmin,
@@ -394,12 +384,18 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
             uint32_t U[SLOTS][D], L[SLOTS][D];
             unsigned ready = 0;   // slots whose bounds are in U, L
             int best = wcount;
+            // keys hold excesses >> qshift; only excesses below the window's widest width matter
+            const uint32_t wmax = wsteps[wcount - 1];
+            const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
             for (long long tc = 0; tc < T && best > 0; tc += 32 * kTileKeys) {
-                // tile level: first width at which a tile can hold a dominator
-                uint32_t key[kTileKeys];
+                // tile level: e_tile = max_i (tmin_i - t_i)^+ bounds every row's excess from
+                // below; a tile matters only while e_tile < delta[best - 1]. Tiles are visited in
+                // ascending order of e_tile (quantized to 24 bits for the key; exact test below).
+                uint32_t key[kTileKeys], ex[kTileKeys];
                 #pragma unroll
                 for (int e = 0; e < kTileKeys; e++) {
                     key[e] = kNoTile;
+                    ex[e] = 0xFFFFFFFFu;
                     const long long tile = tc + 32 * e + lane;
                     if (tile < T) {
                         uint32_t mn[D];
@@ -411,9 +407,9 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
                             emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
                             can |= mn[q] < t[q];
                         }
-                        if (can) {
-                            const int lo = first_wider(wsteps, best, emax);
-                            if (lo < best) key[e] = ((uint32_t)lo << 16) | (uint32_t)(32 * e + lane);
+                        if (can && emax < wsteps[best - 1]) {
+                            ex[e] = emax;
+                            key[e] = (min(emax >> qshift, 0xFFFFFFu) << 8) | (uint32_t)(32 * e + lane);
                         }
                     }
                 }
@@ -423,10 +419,18 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
                     #pragma unroll
                     for (int e = 1; e < kTileKeys; e++) lm = min(lm, key[e]);
                     const uint32_t mkey = __reduce_min_sync(kFull, lm);
-                    if (mkey == kNoTile || (int)(mkey >> 16) >= best) break;
+                    if (mkey == kNoTile) break;
+                    const uint32_t wlim = wsteps[best - 1];
+                    if ((mkey >> 8) > min(wlim >> qshift, 0xFFFFFFu)) break;   // every tile left is too far
+                    uint32_t mine = 0xFFFFFFFFu;
                     #pragma unroll
-                    for (int e = 0; e < kTileKeys; e++) key[e] = key[e] == mkey ? kNoTile : key[e];
-                    const long long r0 = (tc + (mkey & 0xFFFFu)) * kTileRows;
+                    for (int e = 0; e < kTileKeys; e++) {
+                        if (key[e] == mkey) { mine = ex[e]; key[e] = kNoTile; }
+                    }
+                    const uint32_t off = mkey & 0xFFu;
+                    const uint32_t etile = __shfl_sync(kFull, mine, off & 31u);
+                    if (etile >= wlim) continue;
+                    const long long r0 = (tc + off) * kTileRows;
                     // candidate level: lane r looks at row r of the tile
                     uint32_t s[D];
                     if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
@@ -438,20 +442,28 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
                         can_r |= s[q] < t[q];
                     }
                     n_checks += 32;
-                    // a row can dominate t first at its first width wider than e_r;
-                    // it matters only if that width comes before best
-                    uint32_t ckey = 0xFFFFFFFFu;
-                    if (can_r && e_r < wsteps[best - 1])
-                        ckey = ((uint32_t)first_wider(wsteps, best, e_r) << 5) | (uint32_t)lane;
+                    // a row can dominate t only at widths wider than e_r; it matters only if such
+                    // a width comes before best. Rows are taken in ascending order of e_r.
+                    uint32_t ckey = (can_r && e_r < wlim) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
+                                                          : 0xFFFFFFFFu;
                     for (;;) {
                         const uint32_t ck = __reduce_min_sync(kFull, ckey);
-                        if (ck == 0xFFFFFFFFu || (int)(ck >> 5) >= best) break;
+                        if (ck == 0xFFFFFFFFu) break;
                         const int c = (int)(ck & 31u);
                         if (lane == c) ckey = 0xFFFFFFFFu;
+                        const uint32_t ec = __shfl_sync(kFull, e_r, c);
+                        if (ec >= wsteps[best - 1]) {
+                            if ((ck >> 5) > min(wsteps[best - 1] >> qshift, 0x7FFFFFFu)) break;
+                            continue;
+                        }
                         uint32_t sc[D];
                         #pragma unroll
                         for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
-                        const int jlo = (int)(ck >> 5) >> 5, jhi = (best - 1) >> 5;
+                        // first slot holding a width wider than ec
+                        int jlo = 0;
+                        #pragma unroll
+                        for (int j = 0; j < SLOTS - 1; j++) jlo += (32 * j + 31 < wcount && wsteps[32 * j + 31] <= ec) ? 1 : 0;
+                        const int jhi = (best - 1) >> 5;
                         #pragma unroll
                         for (int j = 0; j < SLOTS; j++) {
                             if (j < jlo || j > jhi) continue;
@@ -485,7 +497,9 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
                                 break;
                             }
                         }
+                        if (best == 0) break;
                     }
+                    if (best == 0) break;
                 }
             }
             __syncwarp();
