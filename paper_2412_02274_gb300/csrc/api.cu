@@ -191,6 +191,7 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.sky_rows = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.cand = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.tmin = static_cast<uint32_t *>(take(4 * DP * tiles));
+    w.smin = static_cast<uint32_t *>(take(4 * DP * (tiles / 32 + 1)));
     w.perm = static_cast<uint32_t *>(take(4 * nn));
     w.res = static_cast<int32_t *>(take(4 * nn));
     w.steps = static_cast<uint32_t *>(take(4 * (size_t)(k > 0 ? k : 1)));

@@ -44,6 +44,8 @@ struct WsHeader {
     unsigned int sorted_sel;      // buffer (0/1) holding the last radix sort's result
     unsigned int lo[kMaxD];       // per-attribute canonical minimum over the skyline
     unsigned int hi[kMaxD];       // per-attribute canonical maximum over the skyline
+    unsigned int slo[kMaxD];      // per-attribute canonical minimum over the survivors
+    unsigned int shi[kMaxD];      // per-attribute canonical maximum over the survivors
     unsigned int pad[5];
 };
 
@@ -73,6 +75,7 @@ struct Workspace {
     uint32_t *sky_rows;           // (n + tile) * DP canonical rows, skyline order
     uint32_t *cand;               // (n + tile) * DP canonical rows, partition order
     uint32_t *tmin;               // tiles * DP per-tile minima
+    uint32_t *smin;               // super-tiles (1024 rows) * DP minima
     uint32_t *perm;               // n: partition position -> skyline position
     int32_t *res;                 // n: result per partition position
     uint32_t *steps;              // K widths

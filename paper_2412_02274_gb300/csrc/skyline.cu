@@ -10,13 +10,13 @@
 //               most R rows below it), then sorted by (f, row). Those
 //               dominated by another representative are dropped.
 //   3. filter:  every row, in input order, against the representatives.
-//   4. sort:    the survivors by (f, row) -- the sort-filter-skyline order
-//               (cited in Sec. 4): a survivor can only be dominated by an
-//               earlier one.
-//   5. final:   each survivor against every EARLIER survivor; it is in the
-//               skyline iff none dominates it. (If t is dominated, a skyline
-//               tuple with a smaller f dominates it, and skyline tuples
-//               always survive step 3.)
+//   4. group:   the survivors in a spatial order (16-bit Morton code over
+//               their bounding box) in 32-row tiles with per-tile and
+//               per-1024-row minima.
+//   5. final:   each survivor against the survivors of every tile whose
+//               minimum is <= it in every attribute; it is in the skyline iff
+//               none dominates it. (If t is dominated, a skyline tuple
+//               dominates it, and skyline tuples always survive step 3.)
 //   6. flags by original row -> ascending row numbers, plus the canonical
 //      skyline rows for the gres stage.
 #include "gres_internal.cuh"
@@ -80,6 +80,24 @@ __device__ __forceinline__ bool dominates(const uint32_t (&s)[D], const uint32_t
     return le && lt;
 }
 
+// Morton code of x - lo over `bits` bits per attribute (D * bits <= 32):
+// coordinate i is quantized to floor((x_i - lo_i) 2^bits / (hi_i - lo_i + 1)).
+template <int D>
+__device__ __forceinline__ uint32_t morton(const uint32_t (&x)[D], const uint32_t *lo, const uint32_t *hi, int bits) {
+    uint32_t q[D];
+    #pragma unroll
+    for (int i = 0; i < D; i++) {
+        const unsigned long long span = (unsigned long long)(hi[i] - lo[i]) + 1ull;
+        q[i] = (uint32_t)(((unsigned long long)(x[i] - lo[i]) << bits) / span);
+    }
+    uint32_t key = 0;
+    for (int b = bits - 1; b >= 0; b--) {
+        #pragma unroll
+        for (int i = 0; i < D; i++) key = (key << 1) | ((q[i] >> b) & 1u);
+    }
+    return key;
+}
+
 // Exclusive scan over a kCT-thread block; *total gets the block sum.
 __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *total) {
     __shared__ uint32_t wsum[kCT / 32];
@@ -120,6 +138,8 @@ __global__ void k_init(WsHeader *h, long long n) {
     if (threadIdx.x < kMaxD) {
         h->lo[threadIdx.x] = 0xFFFFFFFFu;
         h->hi[threadIdx.x] = 0u;
+        h->slo[threadIdx.x] = 0xFFFFFFFFu;
+        h->shi[threadIdx.x] = 0u;
     }
 }
 
@@ -257,36 +277,45 @@ __global__ void k_sel_gather(const unsigned long long *keys, long long n, WsHead
     }
 }
 
-// Sorts the candidates by (f, row) (bitonic, one block) and writes their
-// canonical rows to `rows` in that order.
+// Orders the candidates spatially -- by the Morton code of their rows over the
+// candidates' bounding box, then by row -- with a bitonic sort in one block,
+// and writes their canonical rows to `rows` in that order. Spatially tight
+// runs of 32 representatives let the filter skip whole runs.
 template <int D>
 __global__ void __launch_bounds__(kMaxReps)
 k_rep_sort(const uint32_t *data, int dir, const unsigned long long *rep_key, const uint32_t *rep_idx,
            WsHeader *h, uint32_t *rows) {
     __shared__ unsigned long long sk[kMaxReps];
-    __shared__ uint32_t si[kMaxReps];
+    __shared__ uint32_t lo[D], hi[D];
     const int tid = threadIdx.x;
     const int nc = (int)min((long long)h->n_cand, (long long)kMaxReps);
-    sk[tid] = tid < nc ? rep_key[tid] : ~0ull;
-    si[tid] = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
+    if (tid < D) { lo[tid] = 0xFFFFFFFFu; hi[tid] = 0u; }
+    __syncthreads();
+    uint32_t x[D];
+    const uint32_t idx = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
+    if (tid < nc) {
+        load_canon<D>(data, idx, dir, x);
+        #pragma unroll
+        for (int q = 0; q < D; q++) { atomicMin(&lo[q], x[q]); atomicMax(&hi[q], x[q]); }
+    }
+    __syncthreads();
+    const int bits = min(16, 32 / D);
+    sk[tid] = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 32) | idx : ~0ull;
     __syncthreads();
     for (int size = 2; size <= kMaxReps; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             const int j = tid ^ stride;
             if (j > tid) {
                 const bool asc = (tid & size) == 0;
-                const bool gt = sk[tid] > sk[j] || (sk[tid] == sk[j] && si[tid] > si[j]);
-                if (gt == asc) {
+                if ((sk[tid] > sk[j]) == asc) {
                     unsigned long long tk = sk[tid]; sk[tid] = sk[j]; sk[j] = tk;
-                    uint32_t ti = si[tid]; si[tid] = si[j]; si[j] = ti;
                 }
             }
             __syncthreads();
         }
     }
     if (tid < nc) {
-        uint32_t x[D];
-        load_canon<D>(data, si[tid], dir, x);
+        load_canon<D>(data, (uint32_t)(sk[tid] & 0xFFFFFFFFull), dir, x);
         store_row<D>(rows, tid, x);
     }
     if (tid == 0) h->n_cand = nc;
@@ -353,26 +382,40 @@ k_rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
 }
 
 // Survivor flags (not dominated by any representative), rows in input order,
-// plus per-block counts for the compaction. Each warp loads 32 rows (one per
-// lane), then takes them one at a time and tests the row against 32
-// representatives per iteration (lanes over representatives, stopping at the
-// first dominating one).
+// plus per-block counts for the compaction. The representatives sit in shared
+// memory (attribute-major) in runs of 32 with each run's per-attribute
+// minimum; a run can hold a dominator of x only if its minimum is <= x in
+// every attribute. Each warp loads 32 rows (one per lane) and takes them one
+// at a time: lanes first test the runs' minima, then the rows of each
+// possible run, stopping at the first dominator.
 template <int D>
 __global__ void __launch_bounds__(kCT)
 k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, const WsHeader *h,
          uint32_t *flags, uint32_t *blocksum) {
-    __shared__ uint32_t rs[D * kMaxReps];   // attribute-major: lane j reads word j (no conflicts)
+    __shared__ uint32_t rs[D * kMaxReps];
+    __shared__ uint32_t rmin[D * (kMaxReps / 32)];
     __shared__ uint32_t cnt;
     const int nr = (int)h->n_reps;
-    for (int j = threadIdx.x; j < nr; j += kCT) {
+    const int nruns = (nr + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < nruns * 32; j += kCT) {
         uint32_t x[D];
-        load_row<D>(reps, j, x);
+        if (j < nr) load_row<D>(reps, j, x);
+        else {
+            #pragma unroll
+            for (int q = 0; q < D; q++) x[q] = kSentinel;
+        }
         #pragma unroll
-        for (int q = 0; q < D; q++) rs[q * kMaxReps + j] = x[q];
+        for (int q = 0; q < D; q++) {
+            rs[q * kMaxReps + j] = x[q];
+            uint32_t m = x[q];
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((j & 31) == 0) rmin[q * (kMaxReps / 32) + (j >> 5)] = m;
+        }
     }
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long b0 = (long long)blockIdx.x * kCB;
     uint32_t mine = 0;
     for (int g = warp; g < kCB / 32; g += kCT / 32) {
@@ -389,17 +432,20 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, const
             uint32_t xs[D];
             #pragma unroll
             for (int q = 0; q < D; q++) xs[q] = __shfl_sync(0xffffffffu, x[q], l);
+            // runs whose minimum is <= xs everywhere (lane = run)
+            bool maybe = lane < nruns;
+            #pragma unroll
+            for (int q = 0; q < D; q++) maybe &= lane < nruns && rmin[q * (kMaxReps / 32) + lane] <= xs[q];
+            unsigned runs = __ballot_sync(0xffffffffu, maybe);
             bool dom = false;
-            for (int j0 = 0; j0 < nr && !dom; j0 += 32) {
-                const int j = j0 + lane;
-                bool hit = false;
-                if (j < nr) {
-                    uint32_t sv[D];
-                    #pragma unroll
-                    for (int q = 0; q < D; q++) sv[q] = rs[q * kMaxReps + j];
-                    hit = dominates<D>(sv, xs);
-                }
-                dom = __any_sync(0xffffffffu, hit);
+            while (runs && !dom) {
+                const int rr = __ffs(runs) - 1;
+                runs &= runs - 1;
+                const int j = rr * 32 + lane;
+                uint32_t sv[D];
+                #pragma unroll
+                for (int q = 0; q < D; q++) sv[q] = rs[q * kMaxReps + j];
+                dom = __any_sync(0xffffffffu, j < nr && dominates<D>(sv, xs));
             }
             if (!dom) alive_mask |= 1u << l;
         }
@@ -451,16 +497,19 @@ k_scan_blocks(uint32_t *blocksum, long long nb, long long *total, WsHeader *h, i
     }
 }
 
-// Survivors in input order: canonical rows, original row numbers, and the
-// (f, position) pairs for the survivor sort (f recomputed from the row).
+// Survivors in input order: canonical rows, original row numbers, and their
+// per-attribute range (slo / shi) for the spatial order.
 template <int D>
 __global__ void __launch_bounds__(kCT)
 k_compact_surv(const uint32_t *data, int dir, long long n, const uint32_t *flags, const uint32_t *blocksum,
-               uint32_t *surv_rows, uint32_t *surv_orig, unsigned long long *keys, uint32_t *vals,
-               WsHeader *h) {
+               uint32_t *surv_rows, uint32_t *surv_orig, WsHeader *h) {
+    __shared__ uint32_t blo[D], bhi[D];
+    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
     uint32_t run = blocksum[blockIdx.x];
     const long long b0 = (long long)blockIdx.x * kCB;
-    unsigned long long kmin = ~0ull, kmax = 0ull;
+    uint32_t lo[D], hi[D];
+    #pragma unroll
+    for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
     #pragma unroll 1
     for (int r = 0; r < kPer; r++) {
         const long long p = b0 + r * kCT + threadIdx.x;
@@ -472,73 +521,159 @@ k_compact_surv(const uint32_t *data, int dir, long long n, const uint32_t *flags
             load_canon<D>(data, p, dir, x);
             store_row<D>(surv_rows, run + ex, x);
             surv_orig[run + ex] = (uint32_t)p;
-            unsigned long long k = 0;
             #pragma unroll
-            for (int q = 0; q < D; q++) k += x[q];
-            keys[run + ex] = k;
-            vals[run + ex] = run + ex;
-            kmin = k < kmin ? k : kmin;
-            kmax = k > kmax ? k : kmax;
+            for (int q = 0; q < D; q++) { lo[q] = min(lo[q], x[q]); hi[q] = max(hi[q], x[q]); }
         }
         run += tot;
     }
-    warp_minmax_atomic(kmin, kmax, h);
-}
-
-// Survivors in sorted order: rows into `out_rows`, original row numbers into
-// `out_orig`.
-template <int D>
-__global__ void k_gather_sorted(const uint32_t *surv_rows, const uint32_t *surv_orig, const uint32_t *vals0,
-                                const uint32_t *vals1, const WsHeader *h, uint32_t *out_rows,
-                                uint32_t *out_orig) {
-    constexpr int DP = padded_dims(D);
-    const long long M = h->n_surv;
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < M;
-         r += (long long)gridDim.x * blockDim.x) {
-        const uint32_t j = vals[r];
-        const uint4 *src = reinterpret_cast<const uint4 *>(surv_rows + (long long)j * DP);
-        uint4 *dst = reinterpret_cast<uint4 *>(out_rows + r * DP);
-        dst[0] = src[0];
-        if (DP == 8) dst[1] = src[1];
-        out_orig[r] = surv_orig[j];
+    #pragma unroll
+    for (int q = 0; q < D; q++) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+            hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+        }
+        if ((threadIdx.x & 31) == 0) { atomicMin(&blo[q], lo[q]); atomicMax(&bhi[q], hi[q]); }
+    }
+    __syncthreads();
+    if (threadIdx.x < D) {
+        atomicMin(&h->slo[threadIdx.x], blo[threadIdx.x]);
+        atomicMax(&h->shi[threadIdx.x], bhi[threadIdx.x]);
     }
 }
 
-// Final filter over survivors in key order: survivor q is a skyline tuple iff
-// no survivor j < q dominates it. One warp per survivor, lanes over 128 earlier
-// survivors per iteration (4 coalesced rows per lane), stopping at the first
-// dominator.
-// Warps take survivors from the last one down, so the longest scans start
-// first. Sets skyflag[original row].
+// Sort keys of the survivors: a 16-bit Morton code over their range.
+template <int D>
+__global__ void k_surv_keys(const uint32_t *surv_rows, WsHeader *h, unsigned long long *keys, uint32_t *vals) {
+    const long long M = h->n_surv;
+    const int bits = 16 / D;
+    const long long lim = ((M + 31) / 32) * 32;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < lim;
+         r += (long long)gridDim.x * blockDim.x) {
+        unsigned long long k = 0;
+        if (r < M) {
+            uint32_t x[D];
+            load_row<D>(surv_rows, r, x);
+            k = morton<D>(x, h->slo, h->shi, bits);
+            keys[r] = k;
+            vals[r] = (uint32_t)r;
+        }
+        warp_minmax_atomic(r < M ? k : ~0ull, r < M ? k : 0ull, h);
+    }
+}
+
+// Survivors in spatial order, padded to whole 32-row tiles with sentinel rows
+// (all ones: never dominate), with each tile's per-attribute minimum (tmin)
+// and each 1024-row super-tile's minimum (smin). One block of 1024 threads per
+// super-tile; warp w builds tile w of it.
+template <int D>
+__global__ void __launch_bounds__(1024)
+k_gather_tiles(const uint32_t *surv_rows, const uint32_t *surv_orig, const uint32_t *vals0,
+               const uint32_t *vals1, const WsHeader *h, uint32_t *out_rows, uint32_t *out_orig,
+               uint32_t *tmin, uint32_t *smin) {
+    constexpr int DP = padded_dims(D);
+    const long long M = h->n_surv;
+    const long long T = (M + kTileRows - 1) / kTileRows;
+    const long long T2 = (T + 31) / 32;
+    if ((long long)blockIdx.x >= T2) return;
+    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
+    __shared__ uint32_t wm[32][DP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long tile = (long long)blockIdx.x * 32 + w;
+    const long long r = tile * kTileRows + lane;
+    uint32_t x[DP];
+    if (r < M) {
+        const uint32_t j = vals[r];
+        const uint4 *src = reinterpret_cast<const uint4 *>(surv_rows + (long long)j * DP);
+        uint4 a = src[0];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        if (DP == 8) { uint4 b = src[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
+        out_orig[r] = surv_orig[j];
+    } else {
+        #pragma unroll
+        for (int q = 0; q < DP; q++) x[q] = kSentinel;
+    }
+    if (tile < T) {
+        uint4 *dst = reinterpret_cast<uint4 *>(out_rows + r * DP);
+        dst[0] = make_uint4(x[0], x[1], x[2], x[3]);
+        if (DP == 8) dst[1] = make_uint4(x[4 % DP], x[5 % DP], x[6 % DP], x[7 % DP]);
+    }
+    #pragma unroll
+    for (int q = 0; q < DP; q++) {
+        uint32_t m = x[q];
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            wm[w][q] = m;
+            if (tile < T) tmin[tile * DP + q] = m;
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        #pragma unroll
+        for (int q = 0; q < DP; q++) {
+            uint32_t m = wm[lane][q];
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) smin[blockIdx.x * DP + q] = m;
+        }
+    }
+}
+
+// Final filter over the survivors in spatial order: survivor x is a skyline
+// tuple iff no survivor dominates it (Def. 1). A tile (32 rows) or super-tile
+// (1024 rows) can hold a dominator only if its minimum is <= x in every
+// attribute -- the grid-dominance pruning of Sec. 3.1 on tiles. One warp per
+// survivor: lanes test 32 super-tile minima, then the 32 tile minima of each
+// possible super-tile, then the 32 rows of each possible tile, stopping at the
+// first dominator. Sets skyflag[original row].
 template <int D>
 __global__ void __launch_bounds__(kTriThreads)
-k_tri(const uint32_t *surv_rows, const uint32_t *surv_orig, const WsHeader *h, uint32_t *skyflag) {
+k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const uint32_t *smin,
+        const WsHeader *h, uint32_t *skyflag) {
     const long long M = h->n_surv;
+    const long long T = (M + kTileRows - 1) / kTileRows;
+    const long long T2 = (T + 31) / 32;
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * kTriThreads + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * kTriThreads) >> 5;
-    for (long long r = wid; r < M; r += nw) {
-        const long long q = M - 1 - r;
+    for (long long q = wid; q < M; q += nw) {
         uint32_t x[D];
-        load_row<D>(surv_rows, q, x);
+        load_row<D>(rows, q, x);
         bool dom = false;
-        for (long long c0 = 0; c0 < q && !dom; c0 += 128) {
-            uint32_t sv[4][D];
-            #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const long long j = c0 + 32 * u + lane;
-                if (j < q) load_row<D>(surv_rows, j, sv[u]);
+        for (long long s0 = 0; s0 < T2 && !dom; s0 += 32) {
+            bool maybe = false;
+            if (s0 + lane < T2) {
+                uint32_t m[D];
+                load_row<D>(smin, s0 + lane, m);
+                maybe = true;
+                #pragma unroll
+                for (int i = 0; i < D; i++) maybe &= m[i] <= x[i];
             }
-            bool hit = false;
-            #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const long long j = c0 + 32 * u + lane;
-                hit |= j < q && dominates<D>(sv[u], x);
+            unsigned supers = __ballot_sync(0xffffffffu, maybe);
+            while (supers && !dom) {
+                const long long sup = s0 + __ffs(supers) - 1;
+                supers &= supers - 1;
+                const long long tile = sup * 32 + lane;
+                bool tmaybe = false;
+                if (tile < T) {
+                    uint32_t m[D];
+                    load_row<D>(tmin, tile, m);
+                    tmaybe = true;
+                    #pragma unroll
+                    for (int i = 0; i < D; i++) tmaybe &= m[i] <= x[i];
+                }
+                unsigned tiles = __ballot_sync(0xffffffffu, tmaybe);
+                while (tiles && !dom) {
+                    const long long t = sup * 32 + __ffs(tiles) - 1;
+                    tiles &= tiles - 1;
+                    uint32_t sv[D];
+                    load_row<D>(rows, t * kTileRows + lane, sv);
+                    dom = __any_sync(0xffffffffu, dominates<D>(sv, x));
+                }
             }
-            dom = __any_sync(0xffffffffu, hit);
         }
-        if (!dom && lane == 0) skyflag[surv_orig[q]] = 1u;
+        if (!dom && lane == 0) skyflag[orig[q]] = 1u;
     }
 }
 
@@ -600,15 +735,17 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum); note_launch();
     k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv, ws.hdr, 1); note_launch();
     k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
-                                                     ws.surv_orig, ws.keys[0], ws.vals[0], ws.hdr); note_launch();
-    e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 5, st);
+                                                     ws.surv_orig, ws.hdr); note_launch();
+    k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0]); note_launch();
+    e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 2, st);
     if (e != cudaSuccess) return e;
-    k_gather_sorted<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1], ws.hdr,
-                                           ws.cand, ws.perm); note_launch();
+    const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
+    k_gather_tiles<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1],
+                                                       ws.hdr, ws.cand, ws.perm, ws.tmin, ws.smin); note_launch();
     e = cudaMemsetAsync(ws.flags, 0, sizeof(uint32_t) * (size_t)n, st);
     if (e != cudaSuccess) return e;
-    k_tri<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
-        ws.cand, ws.perm, ws.hdr, ws.flags); note_launch();
+    k_final<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
+        ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags); note_launch();
     k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum); note_launch();
     k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky, ws.hdr, 0); note_launch();
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
