@@ -245,10 +245,29 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     executed, checks = (int(v) for v in tests.cpu().tolist())
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # stage events: with --graph each timed step replays its own captured graph, whose
+    # captured event records give that step's stage durations
     G.timing_enable(True)
     G.timing_read()
+    graphs = []
+    launches_per_call = None
+    if args.graph:
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(stream)
+        for _ in range(args.steps):
+            g = torch.cuda.CUDAGraph()
+            c0 = G.launch_count()
+            with torch.cuda.graph(g, stream=cap):
+                G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=cap)
+            launches_per_call = G.launch_count() - c0
+            graphs.append(g)
+        torch.cuda.synchronize(dev)
+        for i in range(args.warmup):
+            graphs[i % len(graphs)].replay()
+        torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
     if world > 1:
@@ -258,10 +277,16 @@ def run_ours(args):
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=stream)
+        if graphs:
+            graphs[i].replay()
+        else:
+            G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=stream)
         ends[i].record(stream)
     torch.cuda.synchronize(dev)
     launches = G.launch_count() - launches0
+    if graphs:
+        # replays launch the captured kernels; the library counted them at capture
+        launches = launches_per_call * args.steps
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -342,6 +367,7 @@ def run_ours(args):
                        "effective_tests_per_step": eff, "executed_lane_tests_per_step": executed,
                        "pruning_checks_per_step": checks,
                        "l2": "256 MiB write between timed steps", "seed_per_rank": "rank",
+                       "launch": "cuda graph replay" if args.graph else "direct calls",
                        "parallelism": f"replicas x{world} (one dataset per GPU)"},
             "gres_queries_per_s": world * 1e3 / ms_per_step,
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
@@ -365,6 +391,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action=argparse.BooleanOptionalAction, default=True,
+                    help="each step replays a gres_compute captured in a CUDA graph "
+                         "(--no-graph: direct calls)")
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=512)
     args = ap.parse_args(argv)

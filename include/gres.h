@@ -180,7 +180,9 @@ unsigned long long gres_launch_count(void);
  * record. gres_timing_read waits for the recorded events and writes, for
  * stages 0 .. nstages-1, the summed milliseconds ms[i] and the number of
  * timed intervals launches[i], then clears the record. Events are created on
- * first use (do a warm-up call before timing) and reused afterwards. */
+ * first use (do a warm-up call before timing) and reused afterwards. Inside a
+ * stream capture the records become graph nodes: each replay of the graph
+ * re-records that call's events. */
 gres_status gres_timing_enable(int32_t on);
 gres_status gres_timing_read(double *ms, int64_t *launches, int32_t nstages);
 

@@ -143,11 +143,21 @@ gres_status set_error(gres_status s, const char *msg) { return fail(s, msg); }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Records e on st; inside a stream capture as an external event node, which
+// re-records the event at every replay of the graph.
+void record_stage_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 void stage_begin(int stage, cudaStream_t st) {
     if (!g_timer.on) return;
     cudaEvent_t e = g_timer.next();
     if (!e) return;
-    cudaEventRecord(e, st);
+    record_stage_event(e, st);
     g_timer.open[stage] = e;
 }
 
@@ -155,7 +165,7 @@ void stage_end(int stage, cudaStream_t st) {
     if (!g_timer.on || !g_timer.open[stage]) return;
     cudaEvent_t e = g_timer.next();
     if (!e) return;
-    cudaEventRecord(e, st);
+    record_stage_event(e, st);
     g_timer.pairs.push_back({stage, g_timer.open[stage], e});
     g_timer.open[stage] = nullptr;
 }
@@ -295,10 +305,8 @@ gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t d
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     gres::Workspace ws;
     gres::workspace_layout(n, d, k, d_ws, &ws);
-    cudaError_t e = gres::launch_init(ws, n, st);
+    cudaError_t e = gres::launch_init_steps(ws, n, h_steps, k, st);
     if (e != cudaSuccess) return cuda_fail(e, "init");
-    e = gres::launch_upload_steps(ws, h_steps, k, st);
-    if (e != cudaSuccess) return cuda_fail(e, "steps upload");
     gres::stage_begin(gres::kStageSkyline, st);
     e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st);
     gres::stage_end(gres::kStageSkyline, st);

@@ -42,11 +42,12 @@ struct WsHeader {
     unsigned int work_next;       // dynamic work counter of the gres kernel
     unsigned int status;          // kStatus* bits
     unsigned int sorted_sel;      // buffer (0/1) holding the last radix sort's result
+    unsigned int done[4];         // block tickets of the last-block-done fusions
     unsigned int lo[kMaxD];       // per-attribute canonical minimum over the skyline
     unsigned int hi[kMaxD];       // per-attribute canonical maximum over the skyline
     unsigned int slo[kMaxD];      // per-attribute canonical minimum over the survivors
     unsigned int shi[kMaxD];      // per-attribute canonical maximum over the survivors
-    unsigned int pad[5];
+    unsigned int pad[1];
 };
 
 // Digit passes that do work in the radix sort of the current key range; the
@@ -87,6 +88,81 @@ int64_t sort_blocks(int64_t n);
 int64_t scan_blocks(int64_t n);
 size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws);
 
+// Resets the per-call header fields (one thread block, >= 32 threads).
+__device__ __forceinline__ void init_header(WsHeader *h, long long n) {
+    if (threadIdx.x == 0) {
+        h->key_min = ~0ull;
+        h->key_max = 0ull;
+        h->n_rows = n;
+        h->n_surv = 0;
+        h->n_sky = 0;
+        h->n_reps = 0;
+        h->n_cand = 0;
+        h->work_next = 0;
+        h->status = 0;
+        h->sorted_sel = 0;
+    }
+    if (threadIdx.x < 4) h->done[threadIdx.x] = 0;
+    if (threadIdx.x < kMaxD) {
+        h->lo[threadIdx.x] = 0xFFFFFFFFu;
+        h->hi[threadIdx.x] = 0u;
+        h->slo[threadIdx.x] = 0xFFFFFFFFu;
+        h->shi[threadIdx.x] = 0u;
+    }
+}
+
+// Last-block-done: every block calls this once at its end (all threads); it
+// returns true in exactly one block, the last to arrive, after which the
+// writes of every other block are visible to it. The ticket is reset for the
+// next launch. No block waits on another.
+__device__ __forceinline__ bool last_block_done(unsigned int *ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = t == gridDim.x * gridDim.y * gridDim.z - 1;
+        if (last) *ticket = 0;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Exclusive scan of a[0 .. count) in place by one block (blockDim.x a
+// multiple of 32, <= 1024); returns the total (in every thread).
+__device__ __forceinline__ uint32_t block_scan_inplace(uint32_t *a, long long count) {
+    __shared__ uint32_t wsum[32];
+    const int nt = blockDim.x;
+    const long long chunk = (count + nt - 1) / nt;
+    const long long c0 = (long long)threadIdx.x * chunk;
+    const long long c1 = c0 + chunk < count ? c0 + chunk : count;
+    uint32_t local = 0;
+    for (long long i = c0; i < c1; i++) local += a[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = local;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int j = 0; j < (nt >> 5); j++) {
+        before += j < w ? wsum[j] : 0u;
+        all += wsum[j];
+    }
+    uint32_t run = before + incl - local;
+    for (long long i = c0; i < c1; i++) {
+        const uint32_t c = a[i];
+        a[i] = run;
+        run += c;
+    }
+    __syncthreads();
+    return all;
+}
+
 // Granlund & Montgomery (1994), unsigned division by a run-time invariant
 // divisor (their Fig. 4.1): with l = ceil(log2 delta),
 // m = floor(2^32 (2^l - delta) / delta) + 1, s1 = min(l, 1), s2 = max(l - 1, 0),
@@ -115,7 +191,8 @@ void stage_end(int stage, cudaStream_t st);
 
 // ---- kernel launchers (each queues on `st`, returns the launch error) -------
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
-cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, cudaStream_t st);
+// Uploads the widths and their division constants and resets the header.
+cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st);
 cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
                               int max_passes, cudaStream_t st);
 cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,

@@ -58,7 +58,8 @@ struct StepChunk {
     uint4 e[kStepChunk];   // (m, s1, s2, delta)
 };
 
-__global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic) {
+__global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n) {
+    if (h) init_header(h, n);
     for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
         const uint4 v = c.e[i];
         steps[c.off + i] = v.w;
@@ -102,47 +103,6 @@ __device__ __forceinline__ void ldg_row(const uint32_t *base, long long r, uint3
     }
 }
 
-// Per-attribute range of the skyline (for the partition coordinates) and a
-// reset of the sort-key range for the partition sort.
-template <int D>
-__global__ void k_sky_range(const uint32_t *sky_rows, WsHeader *h) {
-    const long long S = h->n_sky;
-    uint32_t lo[D], hi[D];
-    #pragma unroll
-    for (int i = 0; i < D; i++) { lo[i] = 0xFFFFFFFFu; hi[i] = 0u; }
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < S;
-         j += (long long)gridDim.x * blockDim.x) {
-        uint32_t x[D];
-        ld_row<D>(sky_rows, j, x);
-        #pragma unroll
-        for (int i = 0; i < D; i++) { lo[i] = min(lo[i], x[i]); hi[i] = max(hi[i], x[i]); }
-    }
-    __shared__ uint32_t blo[D], bhi[D];
-    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
-    __syncthreads();
-    #pragma unroll
-    for (int i = 0; i < D; i++) {
-        #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[i] = min(lo[i], __shfl_xor_sync(kFull, lo[i], o));
-            hi[i] = max(hi[i], __shfl_xor_sync(kFull, hi[i], o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&blo[i], lo[i]);
-            atomicMax(&bhi[i], hi[i]);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < D) {
-        atomicMin(&h->lo[threadIdx.x], blo[threadIdx.x]);
-        atomicMax(&h->hi[threadIdx.x], bhi[threadIdx.x]);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        h->key_min = ~0ull;
-        h->key_max = 0ull;
-    }
-}
-
 __global__ void k_reset_keyrange(WsHeader *h) {
     h->key_min = ~0ull;
     h->key_max = 0ull;
@@ -153,7 +113,6 @@ struct PartArgs {
     int m;           // GRID / ANGULAR slices
     int p;           // SLICED partitions
     int dim;         // SLICED attribute
-    int sec;         // attribute of the order inside a partition
     unsigned long long thr[64];   // ANGULAR: tan^2(j pi / 2m) * 2^32, j = 1 .. m-1
 };
 
@@ -182,12 +141,24 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&x)[D], int q) {
     return v;
 }
 
-// Order inside a partition: attribute `sec` of x = v - lo, scaled to 16 bits
-// of its range (so that a sort key stays within 32 bits for up to 2^16 cells).
+// Order inside a partition: a 16-bit Morton code of x = v - lo over the
+// skyline's range (16 / D bits per attribute), so that 32 consecutive rows of a
+// partition are spatially tight.
 template <int D>
-__device__ __forceinline__ unsigned long long sec16(const uint32_t (&x)[D], const WsHeader *h, int sec) {
-    const unsigned long long span = (unsigned long long)(h->hi[sec] - h->lo[sec]) + 1ull;
-    return ((unsigned long long)pick<D>(x, sec) << 16) / span;
+__device__ __forceinline__ unsigned long long morton16(const uint32_t (&x)[D], const WsHeader *h) {
+    const int bits = 16 / D;
+    uint32_t q[D];
+    #pragma unroll
+    for (int i = 0; i < D; i++) {
+        const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
+        q[i] = (uint32_t)(((unsigned long long)x[i] << bits) / span);
+    }
+    unsigned long long key = 0;
+    for (int b = bits - 1; b >= 0; b--) {
+        #pragma unroll
+        for (int i = 0; i < D; i++) key = (key << 1) | ((q[i] >> b) & 1u);
+    }
+    return key;
 }
 
 // Partition numbers (Sec. 3.1) on coordinates x = v - lo (canonical):
@@ -196,7 +167,7 @@ __device__ __forceinline__ unsigned long long sec16(const uint32_t (&x)[D], cons
 //            thresholds j pi / 2m reached, decided exactly as
 //            (Y << 32) >= X * thr_j in 128-bit integers (Eq. 1)
 //   SLICED:  first pass keys on x_dim; the slice comes from the rank.
-// Sort key = partition << 16 | sec16 (order inside a partition), value = row.
+// Sort key = partition << 16 | morton16 (order inside a partition), value = row.
 template <int D>
 __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                             unsigned long long *keys, uint32_t *vals) {
@@ -222,7 +193,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                     pid += ((unsigned long long)x[i] * (unsigned long long)a.m) / span * w;
                     w *= (unsigned long long)a.m;
                 }
-                key = (pid << 16) | sec16(x, h, a.sec);
+                key = (pid << 16) | morton16<D>(x, h);
             } else if (a.scheme == GRES_PART_ANGULAR) {
                 unsigned long long w = 1;
                 #pragma unroll
@@ -239,7 +210,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                     pid += (unsigned long long)bin * w;
                     w *= (unsigned long long)a.m;
                 }
-                key = (pid << 16) | sec16(x, h, a.sec);
+                key = (pid << 16) | morton16<D>(x, h);
             } else {  // SLICED, first pass
                 key = pick<D>(x, a.dim);
             }
@@ -254,7 +225,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
 
 // SLICED second pass (after k_reset_keyrange): the row of rank r in the
 // order of x_dim falls in slice floor(r p / S) (Sec. 3.1); the new key orders
-// rows by (slice, sec16). Reads the sorted buffer, writes buffer 0 at the same
+// rows by (slice, morton16). Reads the sorted buffer, writes buffer 0 at the same
 // index (in place when the sorted buffer is buffer 0).
 template <int D>
 __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
@@ -276,7 +247,7 @@ __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
             uint32_t xr[D];
             #pragma unroll
             for (int q = 0; q < D; q++) xr[q] = x[q] - h->lo[q];
-            key = (slice << 16) | sec16(xr, h, a.sec);
+            key = (slice << 16) | morton16<D>(xr, h);
         }
         if (valid) {
             keys0[r] = key;
@@ -339,7 +310,8 @@ struct DomArgs {
     const uint32_t *magic;    // K * 4: (m, s1, s2, delta)
     const uint32_t *steps;    // K widths
     WsHeader *hdr;
-    int32_t *res;             // per partition position
+    const uint32_t *perm;     // partition position -> skyline position
+    int32_t *out;             // result per skyline position
     unsigned long long *tests;
     int K;
     int dir;
@@ -505,7 +477,7 @@ __device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *
             __syncwarp();
             if (best < wcount) { result = w0 + best; break; }
         }
-        if (lane == 0) a.res[i] = result;
+        if (lane == 0) a.out[a.perm[i]] = result;
     }
     if (a.tests && lane == 0 && (n_tests | n_checks)) {
         atomicAdd(a.tests, n_tests);
@@ -540,13 +512,6 @@ k_dominance(DomArgs a) {
     } else {
         dom_warp_loop<D, SLOTS, false>(a, a.cand, a.tmin, wsteps, S, T);
     }
-}
-
-__global__ void k_scatter_res(const int32_t *res, const uint32_t *perm, const WsHeader *h, int32_t *out) {
-    const long long S = h->n_sky;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S;
-         i += (long long)gridDim.x * blockDim.x)
-        out[perm[i]] = res[i];
 }
 
 __global__ void k_gproj(const uint32_t *v, long long count, StepChunk c, uint32_t *out) {
@@ -592,7 +557,6 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
                           int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
     const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count);
     stage_begin(kStagePartition, st);
-    k_sky_range<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr); note_launch();
     const int scheme = cfg.scheme;
     PartArgs pa;
     std::memset(&pa, 0, sizeof(pa));
@@ -600,7 +564,6 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     pa.m = cfg.m;
     pa.p = cfg.p;
     pa.dim = cfg.slice_dim;
-    pa.sec = D > 1 ? (scheme == GRES_PART_SLICED ? (cfg.slice_dim + 1) % D : 0) : 0;
     if (scheme == GRES_PART_ANGULAR) {
         const double pi = 3.14159265358979323846;
         for (int j = 1; j < cfg.m && j < 64; j++) {
@@ -637,7 +600,8 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     a.magic = ws.magic;
     a.steps = ws.steps;
     a.hdr = ws.hdr;
-    a.res = ws.res;
+    a.perm = ws.perm;
+    a.out = d_step_idx;
     a.tests = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;
     a.K = k;
     a.dir = dir;
@@ -646,7 +610,6 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     e = launch_dom<D, SLOTS>(a, st);
     stage_end(kStageDominance, st);
     if (e != cudaSuccess) return e;
-    k_scatter_res<<<pb, 256, 0, st>>>(ws.res, ws.perm, ws.hdr, d_step_idx); note_launch();
     return cudaGetLastError();
 }
 
@@ -659,7 +622,7 @@ cudaError_t gres_stage_d(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Wo
 
 }  // namespace
 
-cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, cudaStream_t st) {
+cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st) {
     StepChunk c;
     for (int off = 0; off < k; off += kStepChunk) {
         c.off = off;
@@ -669,7 +632,7 @@ cudaError_t launch_upload_steps(Workspace &ws, const uint32_t *h_steps, int k, c
             udiv_magic(h_steps[off + i], &m, &s1, &s2);
             c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
         }
-        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic); note_launch();
+        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic, off == 0 ? ws.hdr : nullptr, (long long)n); note_launch();
     }
     return cudaGetLastError();
 }

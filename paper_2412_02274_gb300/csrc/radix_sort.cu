@@ -5,8 +5,8 @@
 // digit passes that do any work, E = ceil(bits(key_max - key_min) / 8), is
 // decided on the device: passes p >= E return at once. Pass p reads buffer
 // p & 1 and writes buffer (p + 1) & 1, so the result is in buffer E & 1,
-// which a last one-thread kernel records in hdr->sorted_sel. Digits are
-// taken from key - key_min.
+// which the first kernel records in hdr->sorted_sel. Digits are taken from
+// key - key_min.
 //
 // Each pass is three kernels: per-block digit histograms, a per-digit scan
 // over the blocks (one block per digit, with the digit totals), and a stable
@@ -27,6 +27,7 @@ constexpr int kWarps = kThreads / 32;
 
 __global__ void __launch_bounds__(kThreads)
 k_hist(WsHeader *h, const unsigned long long *keys_in, uint32_t *hist, const long long *d_n, int pass) {
+    if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0) h->sorted_sel = (unsigned)(radix_passes(h) & 1);
     if (pass >= radix_passes(h)) return;
     const long long n = *d_n;
     const long long G = (n + kTile - 1) / kTile;
@@ -154,8 +155,6 @@ k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_i
     }
 }
 
-__global__ void k_sort_done(WsHeader *h) { h->sorted_sel = (unsigned)(radix_passes(h) & 1); }
-
 }  // namespace
 
 int64_t sort_blocks(int64_t n) { return (n + kTile - 1) / kTile; }
@@ -165,18 +164,15 @@ int64_t sort_blocks(int64_t n) { return (n + kTile - 1) / kTile; }
 cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
                               int max_passes, cudaStream_t st) {
     const int64_t G = sort_blocks(n_max);
-    if (G == 0) {
-        k_sort_done<<<1, 1, 0, st>>>(ws.hdr); note_launch();
-        return cudaGetLastError();
+    if (G > 0) {
+        for (int p = 0; p < max_passes; p++) {
+            const int in = p & 1, out = (p + 1) & 1;
+            k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p); note_launch();
+            k_scan<<<256, kScanThreads, 0, st>>>(ws.hdr, ws.hist, ws.dtot, d_n, p); note_launch();
+            k_scatter<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.vals[in], ws.keys[out],
+                                                        ws.vals[out], ws.hist, ws.dtot, d_n, p); note_launch();
+        }
     }
-    for (int p = 0; p < max_passes; p++) {
-        const int in = p & 1, out = (p + 1) & 1;
-        k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p); note_launch();
-        k_scan<<<256, kScanThreads, 0, st>>>(ws.hdr, ws.hist, ws.dtot, d_n, p); note_launch();
-        k_scatter<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.vals[in], ws.keys[out],
-                                                    ws.vals[out], ws.hist, ws.dtot, d_n, p); note_launch();
-    }
-    k_sort_done<<<1, 1, 0, st>>>(ws.hdr); note_launch();
     return cudaGetLastError();
 }
 

@@ -122,26 +122,7 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *total) {
     return before + incl - v;
 }
 
-__global__ void k_init(WsHeader *h, long long n) {
-    if (threadIdx.x == 0) {
-        h->key_min = ~0ull;
-        h->key_max = 0ull;
-        h->n_rows = n;
-        h->n_surv = 0;
-        h->n_sky = 0;
-        h->n_reps = 0;
-        h->n_cand = 0;
-        h->work_next = 0;
-        h->status = 0;
-        h->sorted_sel = 0;
-    }
-    if (threadIdx.x < kMaxD) {
-        h->lo[threadIdx.x] = 0xFFFFFFFFu;
-        h->hi[threadIdx.x] = 0u;
-        h->slo[threadIdx.x] = 0xFFFFFFFFu;
-        h->shi[threadIdx.x] = 0u;
-    }
-}
+__global__ void k_init(WsHeader *h, long long n) { init_header(h, n); }
 
 __device__ __forceinline__ void warp_minmax_atomic(unsigned long long kmin, unsigned long long kmax,
                                                    WsHeader *h) {
@@ -186,35 +167,13 @@ __device__ __forceinline__ int sel_shift1(const WsHeader *h) {
     return bits > 12 ? bits - 12 : 0;
 }
 
-__global__ void k_sel_hist(const unsigned long long *keys, long long n, const WsHeader *h, int level,
-                           uint32_t *hist) {
-    __shared__ uint32_t sh[kSelBuckets];
-    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
-    __syncthreads();
-    const unsigned long long kmin = h->key_min;
-    const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
-    const unsigned long long b1 = h->sel_b1;
-    const bool active = level == 1 || b1 < kSelBuckets;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; active && i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long kn = keys[i] - kmin;
-        if (level == 1) {
-            atomicAdd(&sh[kn >> sh1], 1u);
-        } else if ((kn >> sh1) == b1) {
-            atomicAdd(&sh[(kn >> sh2) & ((1ull << (sh1 - sh2)) - 1ull)], 1u);
-        }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
-        if (sh[b]) atomicAdd(&hist[b], sh[b]);
-}
-
-// One block of 1024 threads: first bucket at which the running count (plus
+// Run by the last block of k_sel_hist (1024 threads): first bucket at which
+// the running count (plus
 // `below` for level 2) exceeds R. Level 1 writes sel_b1 and sel_below (the
 // count under bucket b1; sel_b1 = 4096 when every row fits); level 2 writes
 // the final threshold sel_thr in units of 2^sh2 (rows with
 // (f - f_min) >> sh2 < sel_thr are representatives: at most R of them).
-__global__ void __launch_bounds__(1024) k_sel_find(const uint32_t *hist, int level, int R, WsHeader *h) {
+__device__ __forceinline__ void sel_find(const uint32_t *hist, int level, int R, WsHeader *h) {
     __shared__ uint32_t wsum[32];
     __shared__ unsigned long long found;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -257,6 +216,30 @@ __global__ void __launch_bounds__(1024) k_sel_find(const uint32_t *hist, int lev
             h->sel_thr = ((unsigned long long)h->sel_b1 << (sh1 - sh2)) + b2;
         }
     }
+}
+
+__global__ void __launch_bounds__(1024)
+k_sel_hist(const unsigned long long *keys, long long n, WsHeader *h, int level, uint32_t *hist, int R) {
+    __shared__ uint32_t sh[kSelBuckets];
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    const unsigned long long kmin = h->key_min;
+    const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
+    const unsigned long long b1 = h->sel_b1;
+    const bool active = level == 1 || b1 < kSelBuckets;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; active && i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long kn = keys[i] - kmin;
+        if (level == 1) {
+            atomicAdd(&sh[kn >> sh1], 1u);
+        } else if ((kn >> sh1) == b1) {
+            atomicAdd(&sh[(kn >> sh2) & ((1ull << (sh1 - sh2)) - 1ull)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    if (last_block_done(&h->done[0])) sel_find(hist, level, R, h);
 }
 
 // Rows under the threshold, appended in any order (sorted next).
@@ -321,48 +304,12 @@ k_rep_sort(const uint32_t *data, int dir, const unsigned long long *rep_key, con
     if (tid == 0) h->n_cand = nc;
 }
 
-// Representatives dominated by another one are dropped (Sec. 3.1). One warp
-// per candidate, lanes over the other candidates (all staged in shared
-// memory by every block).
-constexpr int kRepBlock = 1024;
+// Keeps the non-dominated candidates, in order, in place (run by the last
+// block of k_rep_flags, 1024 threads).
 template <int D>
-__global__ void __launch_bounds__(kRepBlock)
-k_rep_flags(const uint32_t *cand_rows, const WsHeader *h, uint32_t *rep_flag) {
-    __shared__ uint32_t rows[D * kMaxReps];
-    const int nc = (int)h->n_cand;
-    for (int i = threadIdx.x; i < nc; i += kRepBlock) {
-        uint32_t x[D];
-        load_row<D>(cand_rows, i, x);
-        #pragma unroll
-        for (int q = 0; q < D; q++) rows[q * kMaxReps + i] = x[q];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (kRepBlock / 32) + (threadIdx.x >> 5);
-    if (i >= nc) return;
-    uint32_t x[D];
-    #pragma unroll
-    for (int q = 0; q < D; q++) x[q] = rows[q * kMaxReps + i];
-    bool dom = false;
-    for (int j0 = 0; j0 < nc && !dom; j0 += 32) {
-        const int j = j0 + lane;
-        bool hit = false;
-        if (j < nc) {
-            uint32_t sv[D];
-            #pragma unroll
-            for (int q = 0; q < D; q++) sv[q] = rows[q * kMaxReps + j];
-            hit = dominates<D>(sv, x);
-        }
-        dom = __any_sync(0xffffffffu, hit);
-    }
-    if (lane == 0) rep_flag[i] = dom ? 0u : 1u;
-}
-
-// Keeps the non-dominated candidates, in order, in place (one block).
-template <int D>
-__global__ void __launch_bounds__(kMaxReps)
-k_rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
+__device__ __forceinline__ void rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
     __shared__ uint32_t wsum[kMaxReps / 32];
+    __syncthreads();
     const int i = threadIdx.x;
     const int nc = (int)h->n_cand;
     const bool keep = i < nc && rep_flag[i] != 0u;
@@ -381,6 +328,45 @@ k_rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
     if (i == 0) h->n_reps = all;
 }
 
+// Representatives dominated by another one are dropped (Sec. 3.1). One warp
+// per candidate, lanes over the other candidates (all staged in shared
+// memory by every block).
+constexpr int kRepBlock = 1024;
+template <int D>
+__global__ void __launch_bounds__(kRepBlock)
+k_rep_flags(uint32_t *cand_rows, WsHeader *h, uint32_t *rep_flag) {
+    __shared__ uint32_t rows[D * kMaxReps];
+    const int nc = (int)h->n_cand;
+    for (int i = threadIdx.x; i < nc; i += kRepBlock) {
+        uint32_t x[D];
+        load_row<D>(cand_rows, i, x);
+        #pragma unroll
+        for (int q = 0; q < D; q++) rows[q * kMaxReps + i] = x[q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kRepBlock / 32) + (threadIdx.x >> 5);
+    if (i < nc) {
+        uint32_t x[D];
+        #pragma unroll
+        for (int q = 0; q < D; q++) x[q] = rows[q * kMaxReps + i];
+        bool dom = false;
+        for (int j0 = 0; j0 < nc && !dom; j0 += 32) {
+            const int j = j0 + lane;
+            bool hit = false;
+            if (j < nc) {
+                uint32_t sv[D];
+                #pragma unroll
+                for (int q = 0; q < D; q++) sv[q] = rows[q * kMaxReps + j];
+                hit = dominates<D>(sv, x);
+            }
+            dom = __any_sync(0xffffffffu, hit);
+        }
+        if (lane == 0) rep_flag[i] = dom ? 0u : 1u;
+    }
+    if (last_block_done(&h->done[1])) rep_compact<D>(cand_rows, rep_flag, h);
+}
+
 // Survivor flags (not dominated by any representative), rows in input order,
 // plus per-block counts for the compaction. The representatives sit in shared
 // memory (attribute-major) in runs of 32 with each run's per-attribute
@@ -390,8 +376,8 @@ k_rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
 // possible run, stopping at the first dominator.
 template <int D>
 __global__ void __launch_bounds__(kCT)
-k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, const WsHeader *h,
-         uint32_t *flags, uint32_t *blocksum) {
+k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHeader *h,
+         uint32_t *flags, uint32_t *blocksum, long long nb) {
     __shared__ uint32_t rs[D * kMaxReps];
     __shared__ uint32_t rmin[D * (kMaxReps / 32)];
     __shared__ uint32_t cnt;
@@ -460,40 +446,14 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, const
     if (lane == 0 && mine) atomicAdd(&cnt, mine);
     __syncthreads();
     if (threadIdx.x == 0) blocksum[blockIdx.x] = cnt;
-}
-
-// Exclusive scan of blocksum[0 .. nb) in place (one block); *total = sum.
-// With reset_keys the sort-key range is cleared for the next key pass.
-__global__ void __launch_bounds__(1024)
-k_scan_blocks(uint32_t *blocksum, long long nb, long long *total, WsHeader *h, int reset_keys) {
-    __shared__ uint32_t wsum[32];
-    const long long chunk = (nb + 1023) / 1024;
-    const long long c0 = (long long)threadIdx.x * chunk;
-    const long long c1 = min(c0 + chunk, nb);
-    uint32_t local = 0;
-    for (long long i = c0; i < c1; i++) local += blocksum[i];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t incl = local;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    uint32_t before = 0, all = 0;
-    for (int j = 0; j < 32; j++) {
-        before += j < w ? wsum[j] : 0u;
-        all += wsum[j];
-    }
-    uint32_t run = before + incl - local;
-    for (long long i = c0; i < c1; i++) {
-        uint32_t c = blocksum[i];
-        blocksum[i] = run;
-        run += c;
-    }
-    if (threadIdx.x == 0) {
-        *total = all;
-        if (reset_keys) { h->key_min = ~0ull; h->key_max = 0ull; }
+    if (last_block_done(&h->done[2])) {
+        // survivors' offsets; the sort-key range is cleared for the survivor sort
+        const uint32_t total = block_scan_inplace(blocksum, nb);
+        if (threadIdx.x == 0) {
+            h->n_surv = total;
+            h->key_min = ~0ull;
+            h->key_max = 0ull;
+        }
     }
 }
 
@@ -542,9 +502,14 @@ k_compact_surv(const uint32_t *data, int dir, long long n, const uint32_t *flags
     }
 }
 
-// Sort keys of the survivors: a 16-bit Morton code over their range.
+// Sort keys of the survivors: a 16-bit Morton code over their range. Also
+// clears the skyline flags.
 template <int D>
-__global__ void k_surv_keys(const uint32_t *surv_rows, WsHeader *h, unsigned long long *keys, uint32_t *vals) {
+__global__ void k_surv_keys(const uint32_t *surv_rows, WsHeader *h, unsigned long long *keys, uint32_t *vals,
+                            uint32_t *skyflag, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        skyflag[i] = 0u;   // cleared for k_final
     const long long M = h->n_surv;
     const int bits = 16 / D;
     const long long lim = ((M + 31) / 32) * 32;
@@ -678,7 +643,7 @@ k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const 
 }
 
 __global__ void __launch_bounds__(kCT)
-k_count_flags(const uint32_t *flags, long long n, uint32_t *blocksum) {
+k_count_flags(const uint32_t *flags, long long n, uint32_t *blocksum, long long nb, WsHeader *h) {
     uint32_t cnt = 0;
     const long long b0 = (long long)blockIdx.x * kCB;
     #pragma unroll
@@ -689,13 +654,25 @@ k_count_flags(const uint32_t *flags, long long n, uint32_t *blocksum) {
     uint32_t tot;
     block_scan(cnt, &tot);
     if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+    if (last_block_done(&h->done[3])) {
+        const uint32_t total = block_scan_inplace(blocksum, nb);
+        if (threadIdx.x == 0) h->n_sky = total;
+    }
 }
 
-// Skyline rows in ascending row order: row numbers and canonical rows.
+// Skyline rows in ascending row order: row numbers, canonical rows, and the
+// skyline's per-attribute range (lo / hi) for the partitioning; the sort-key
+// range is cleared for the partition sort.
 template <int D>
 __global__ void __launch_bounds__(kCT)
 k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyflag,
-              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows) {
+              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows, WsHeader *h) {
+    __shared__ uint32_t blo[D], bhi[D];
+    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { h->key_min = ~0ull; h->key_max = 0ull; }
+    uint32_t lo[D], hi[D];
+    #pragma unroll
+    for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
     uint32_t run = blocksum[blockIdx.x];
     const long long b0 = (long long)blockIdx.x * kCB;
     #pragma unroll 1
@@ -709,8 +686,24 @@ k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyfla
             uint32_t x[D];
             load_canon<D>(data, p, dir, x);
             store_row<D>(sky_rows, run + ex, x);
+            #pragma unroll
+            for (int q = 0; q < D; q++) { lo[q] = min(lo[q], x[q]); hi[q] = max(hi[q], x[q]); }
         }
         run += tot;
+    }
+    #pragma unroll
+    for (int q = 0; q < D; q++) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+            hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+        }
+        if ((threadIdx.x & 31) == 0 && lo[q] <= hi[q]) { atomicMin(&blo[q], lo[q]); atomicMax(&bhi[q], hi[q]); }
+    }
+    __syncthreads();
+    if (threadIdx.x < D && blo[threadIdx.x] <= bhi[threadIdx.x]) {
+        atomicMin(&h->lo[threadIdx.x], blo[threadIdx.x]);
+        atomicMax(&h->hi[threadIdx.x], bhi[threadIdx.x]);
     }
 }
 
@@ -723,33 +716,26 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     cudaError_t e = cudaMemsetAsync(ws.sel_hist, 0, sizeof(uint32_t) * 2 * kSelBuckets, st);
     if (e != cudaSuccess) return e;
     const int hb = (int)std::min<long long>((n + 1023) / 1024, 152LL * 2);
-    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 1, ws.sel_hist); note_launch();
-    k_sel_find<<<1, 1024, 0, st>>>(ws.sel_hist, 1, reps, ws.hdr); note_launch();
-    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 2, ws.sel_hist + kSelBuckets); note_launch();
-    k_sel_find<<<1, 1024, 0, st>>>(ws.sel_hist + kSelBuckets, 2, reps, ws.hdr); note_launch();
+    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 1, ws.sel_hist, reps); note_launch();
+    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 2, ws.sel_hist + kSelBuckets, reps); note_launch();
     k_sel_gather<<<gb, 256, 0, st>>>(ws.keys[0], n, ws.hdr, ws.rep_key, ws.rep_idx); note_launch();
     k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps); note_launch();
     const int r_eff = (int)std::min<int64_t>(reps, n);
     k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(ws.reps, ws.hdr, ws.perm); note_launch();
-    k_rep_compact<D><<<1, kMaxReps, 0, st>>>(ws.reps, ws.perm, ws.hdr); note_launch();
-    k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum); note_launch();
-    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_surv, ws.hdr, 1); note_launch();
+    k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum, nb); note_launch();
     k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
                                                      ws.surv_orig, ws.hdr); note_launch();
-    k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0]); note_launch();
+    k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
     e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 2, st);
     if (e != cudaSuccess) return e;
     const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
     k_gather_tiles<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1],
                                                        ws.hdr, ws.cand, ws.perm, ws.tmin, ws.smin); note_launch();
-    e = cudaMemsetAsync(ws.flags, 0, sizeof(uint32_t) * (size_t)n, st);
-    if (e != cudaSuccess) return e;
     k_final<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
         ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags); note_launch();
-    k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum); note_launch();
-    k_scan_blocks<<<1, 1024, 0, st>>>(ws.blocksum, nb, &ws.hdr->n_sky, ws.hdr, 0); note_launch();
+    k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum, nb, ws.hdr); note_launch();
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
-                                                    ws.sky_rows); note_launch();
+                                                    ws.sky_rows, ws.hdr); note_launch();
     return cudaGetLastError();
 }
 

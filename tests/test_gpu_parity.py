@@ -129,14 +129,17 @@ def test_edge_cases():
     _check(make_dataset("ant", 4000, 8, bits=20, seed=1), steps_log(128, 16))
 
 
-def test_large_skyline_streams_from_global_memory():
-    """A skyline too large for shared memory (d=2, every row on one anti-diagonal)."""
-    n = 16000
-    x = np.arange(n, dtype=np.uint32) * 61
+@pytest.mark.parametrize("n", [16000, 40000])
+def test_large_skyline_streams_from_global_memory(n):
+    """Skylines too large for shared memory (d=2, every row on one anti-diagonal); the
+    40,000-row case also takes the multi-block sorts (more than 16,384 survivors)."""
+    x = np.arange(n, dtype=np.uint32) * 23
     data = np.stack([x, x.max() - x], axis=1).astype(np.uint32)
+    data = data[np.random.default_rng(n).permutation(n)]
     steps = steps_log(48, 20)
     gs, gr = _gpu(data, steps, G.MIN, G.plan(G.PART_GRID))
     assert list(gs) == list(range(n))
+    assert list(O.skyline_allpairs(data[:2000])) == list(range(2000))
     targets = np.linspace(0, n - 1, 97).astype(np.int64)
     exp = O.gres(data, steps, candidates=np.arange(n), targets=targets, threads=THREADS)
     np.testing.assert_array_equal(gr[targets], exp)
