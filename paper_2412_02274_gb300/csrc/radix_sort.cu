@@ -24,6 +24,7 @@ constexpr int kThreads = 256;
 constexpr int kItems = 4;
 constexpr int kTile = kThreads * kItems;   // 1024 items per block
 constexpr int kWarps = kThreads / 32;
+constexpr long long kScanFreeBlocks = 64;   // up to this many blocks, scatter blocks scan for themselves
 
 __global__ void __launch_bounds__(kThreads)
 k_hist(WsHeader *h, const unsigned long long *keys_in, uint32_t *hist, const long long *d_n, int pass) {
@@ -55,6 +56,7 @@ k_scan(WsHeader *h, uint32_t *hist, uint32_t *dtot, const long long *d_n, int pa
     if (pass >= radix_passes(h)) return;
     const long long n = *d_n;
     const long long G = (n + kTile - 1) / kTile;
+    if (G <= kScanFreeBlocks) return;
     uint32_t *row = hist + (long long)blockIdx.x * G;
     __shared__ uint32_t warp_tot[kScanThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -97,8 +99,24 @@ k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_i
     __shared__ uint32_t wsum[kWarps];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     {
-        // digit offsets: exclusive scan of the 256 digit totals
-        const uint32_t v = dtot[tid];
+        // digit offsets: exclusive scan of the 256 digit totals. With few blocks the
+        // totals and this block's offset inside the digit come straight from the
+        // per-block counts (no separate scan kernel).
+        uint32_t v, inner;
+        if (G <= kScanFreeBlocks) {
+            const uint32_t *row = hist + (long long)tid * G;
+            uint32_t tot = 0, pre = 0;
+            for (long long b = 0; b < G; b++) {
+                const uint32_t c = row[b];
+                pre += b < (long long)blockIdx.x ? c : 0u;
+                tot += c;
+            }
+            v = tot;
+            inner = pre;
+        } else {
+            v = dtot[tid];
+            inner = hist[(long long)tid * G + blockIdx.x];
+        }
         uint32_t incl = v;
         #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -110,7 +128,7 @@ k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_i
         uint32_t before = 0;
         #pragma unroll
         for (int j = 0; j < kWarps; j++) before += j < w ? wsum[j] : 0u;
-        base[tid] = before + incl - v + hist[(long long)tid * G + blockIdx.x];
+        base[tid] = before + incl - v + inner;
     }
     for (int j = 0; j < kWarps; j++) wcnt[j][tid] = 0;
     __syncthreads();
@@ -168,7 +186,9 @@ cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n
         for (int p = 0; p < max_passes; p++) {
             const int in = p & 1, out = (p + 1) & 1;
             k_hist<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.hist, d_n, p); note_launch();
-            k_scan<<<256, kScanThreads, 0, st>>>(ws.hdr, ws.hist, ws.dtot, d_n, p); note_launch();
+            if (G > kScanFreeBlocks) {
+                k_scan<<<256, kScanThreads, 0, st>>>(ws.hdr, ws.hist, ws.dtot, d_n, p); note_launch();
+            }
             k_scatter<<<(unsigned)G, kThreads, 0, st>>>(ws.hdr, ws.keys[in], ws.vals[in], ws.keys[out],
                                                         ws.vals[out], ws.hist, ws.dtot, d_n, p); note_launch();
         }

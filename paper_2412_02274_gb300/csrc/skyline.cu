@@ -374,8 +374,9 @@ k_rep_flags(uint32_t *cand_rows, WsHeader *h, uint32_t *rep_flag) {
 // every attribute. Each warp loads 32 rows (one per lane) and takes them one
 // at a time: lanes first test the runs' minima, then the rows of each
 // possible run, stopping at the first dominator.
+constexpr int kFilterThreads = kCB;   // one warp per 32 rows of the block's kCB rows
 template <int D>
-__global__ void __launch_bounds__(kCT)
+__global__ void __launch_bounds__(kFilterThreads)
 k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHeader *h,
          uint32_t *flags, uint32_t *blocksum, long long nb) {
     __shared__ uint32_t rs[D * kMaxReps];
@@ -384,7 +385,7 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
     const int nr = (int)h->n_reps;
     const int nruns = (nr + 31) / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < nruns * 32; j += kCT) {
+    for (int j = threadIdx.x; j < nruns * 32; j += kFilterThreads) {
         uint32_t x[D];
         if (j < nr) load_row<D>(reps, j, x);
         else {
@@ -404,7 +405,7 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
     __syncthreads();
     const long long b0 = (long long)blockIdx.x * kCB;
     uint32_t mine = 0;
-    for (int g = warp; g < kCB / 32; g += kCT / 32) {
+    for (int g = warp; g < kCB / 32; g += kFilterThreads / 32) {
         const long long p = b0 + g * 32 + lane;
         uint32_t x[D];
         if (p < n) load_canon<D>(data, p, dir, x);
@@ -722,7 +723,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps); note_launch();
     const int r_eff = (int)std::min<int64_t>(reps, n);
     k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(ws.reps, ws.hdr, ws.perm); note_launch();
-    k_filter<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum, nb); note_launch();
+    k_filter<D><<<(unsigned)nb, kFilterThreads, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum, nb); note_launch();
     k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
                                                      ws.surv_orig, ws.hdr); note_launch();
     k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
