@@ -159,6 +159,63 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
                               int64_t *h_sky_idx, int32_t *h_step_idx, int64_t *h_sky_count,
                               void *stream);
 
+/* ---- resident datasets and repeated queries --------------------------------
+ * The skyline and its candidate tiles depend only on the data (Def. 1; gres
+ * is stable, Sec. 3.2), so a dataset prepared once answers any number of gres
+ * queries, each with its own step list, with the grid-dominance kernel alone. */
+typedef struct gres_dataset gres_dataset;
+
+/* Prepares `data` (n*d uint32 row-major; on the host when data_on_host != 0,
+ * else on the device) with plan `cfg` (may be NULL): computes the skyline and
+ * the candidate tiles on `stream`, waits for them, and keeps them in device
+ * memory owned by the handle (gres_dataset_info reports its size). Until
+ * gres_dataset_destroy the input may be freed. GRES_ENOMEM if the device
+ * memory runs out. */
+gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int32_t dir,
+                                const gres_plan_cfg *cfg, int32_t data_on_host, void *stream,
+                                gres_dataset **out);
+gres_status gres_dataset_destroy(gres_dataset *ds);
+/* n, d, skyline size S and the handle's device bytes (any output may be NULL). */
+gres_status gres_dataset_info(const gres_dataset *ds, int64_t *n, int32_t *d, int64_t *sky_count,
+                              size_t *device_bytes);
+/* The S skyline row numbers (ascending) into `out` (host if out_on_host, waits). */
+gres_status gres_dataset_sky_idx(const gres_dataset *ds, int64_t *out, int32_t out_on_host, void *stream);
+
+/* Device scratch bytes of one query with k widths. */
+gres_status gres_query_workspace_size(int32_t k, size_t *bytes);
+/* gres of every skyline tuple of a prepared dataset for the widths h_steps
+ * (host, k, strictly ascending, >= 1): d_step_idx[j] (device, S int32) is the
+ * result of skyline row j (same order as gres_dataset_sky_idx). d_qws: device
+ * scratch of gres_query_workspace_size(k) bytes, 256-byte aligned; queries
+ * that overlap on the GPU need distinct scratch. Queues on `stream`. */
+gres_status gres_query(const gres_dataset *ds, const uint32_t *h_steps, int32_t k, void *d_qws,
+                       size_t qws_bytes, int32_t *d_step_idx, void *stream);
+
+/* ---- many independent instances in one call ----------------------------------
+ * Each instance is a whole gres_compute problem. Skyline and partitioning run
+ * per instance on a pool of internal streams forked from and joined back to
+ * `stream`; then the grid-dominance kernel runs once per dimensionality (and
+ * slots setting) over the targets of all those instances. Nothing waits on the
+ * host: the call can be captured into one CUDA graph. */
+typedef struct {
+    const uint32_t *d_data;   /* device, n*d uint32 row-major                    */
+    int64_t n;
+    int32_t d;
+    int32_t dir;
+    const uint32_t *d_steps;  /* device, k widths, strictly ascending, >= 1 (not
+                                 checked on the host in this call)               */
+    int32_t k;
+    gres_plan_cfg cfg;        /* plan (zero fields: defaults)                    */
+    int64_t *d_sky_idx;       /* device, capacity n: skyline rows, ascending     */
+    int32_t *d_step_idx;      /* device, capacity n: result per skyline row      */
+    int64_t *d_sky_count;     /* device (may be NULL): S                         */
+} gres_instance;
+
+/* Device scratch bytes for the instances (sum of their gres_compute needs plus
+ * a small head). */
+gres_status gres_batch_workspace_size(const gres_instance *inst, int32_t n_inst, size_t *bytes);
+gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, size_t ws_bytes, void *stream);
+
 /* Grid projection (Sec. 2) of `count` values at each of k widths:
  * d_out[j*count + i] = floor(d_values[i] / h_steps[j]) (the paper's
  * floor(t[i] g) numerator with delta = 2^B / g). Division by a run-time

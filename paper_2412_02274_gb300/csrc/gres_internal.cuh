@@ -189,6 +189,26 @@ enum Stage { kStageSkyline = 0, kStagePartition = 1, kStageDominance = 2, kStage
 void stage_begin(int stage, cudaStream_t st);
 void stage_end(int stage, cudaStream_t st);
 
+// One gres query on one prepared candidate set.
+struct DomQuery {
+    const uint32_t *cand;     // T*32 rows, DP words each (partition order, sentinel-padded)
+    const uint32_t *tmin;     // T rows, DP words each
+    const uint32_t *perm;     // partition position -> skyline position
+    const long long *n_sky;   // S (device)
+    const uint32_t *magic;    // K * 4: (m, s1, s2, delta)
+    const uint32_t *steps;    // K widths
+    int32_t *out;             // result per skyline position
+    int K;
+    int dir;
+};
+
+// Division constants to make on the device for one query (k_make_magic).
+struct MagicJob {
+    const uint32_t *steps;
+    uint32_t *magic;
+    int K;
+    unsigned *zero;           // a counter to clear (may be null)
+};
 // ---- kernel launchers (each queues on `st`, returns the launch error) -------
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
 // Uploads the widths and their division constants and resets the header.
@@ -201,6 +221,19 @@ cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t *d_sky_idx, int32_t *d_step_idx,
                               unsigned long long *d_tests, cudaStream_t st);
+// The candidate partitioning of the skyline in ws (cand, tmin, perm).
+cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st);
+// The grid-dominance kernel for one query; *counter must be 0.
+cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,
+                             unsigned long long *tests, cudaStream_t st);
+// One launch for up to 256 queries of the same d; *counter must be 0.
+cudaError_t launch_dominance_batch(int d, int slots, const DomQuery *qs, int count, unsigned *counter,
+                                   cudaStream_t st);
+// Device-side division constants (and counter resets) for many queries.
+cudaError_t launch_make_magic(const MagicJob *jobs, int count, cudaStream_t st);
+// Widths from the host into d_steps / d_magic; zeroes *zero when given.
+cudaError_t launch_upload_steps(uint32_t *d_steps, uint32_t *d_magic, unsigned *zero, const uint32_t *h_steps,
+                                int k, cudaStream_t st);
 cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps, int k,
                          uint32_t *d_out, cudaStream_t st);
 

@@ -58,8 +58,10 @@ struct StepChunk {
     uint4 e[kStepChunk];   // (m, s1, s2, delta)
 };
 
-__global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n) {
+__global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n,
+                               unsigned *zero) {
     if (h) init_header(h, n);
+    if (zero && threadIdx.x == 0) *zero = 0u;
     for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
         const uint4 v = c.e[i];
         steps[c.off + i] = v.w;
@@ -305,16 +307,9 @@ __global__ void k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const
 
 // ---- the pairwise grid-dominance kernel ------------------------------------
 struct DomArgs {
-    const uint32_t *cand;     // T*32 rows, DP words each (partition order)
-    const uint32_t *tmin;     // T rows, DP words each
-    const uint32_t *magic;    // K * 4: (m, s1, s2, delta)
-    const uint32_t *steps;    // K widths
-    WsHeader *hdr;
-    const uint32_t *perm;     // partition position -> skyline position
-    int32_t *out;             // result per skyline position
+    DomQuery q;
+    unsigned *counter;        // work counter (zeroed before the launch)
     unsigned long long *tests;
-    int K;
-    int dir;
     int smem_words;           // dynamic shared memory, in words
 };
 
@@ -329,160 +324,152 @@ __host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 
 constexpr int kTileKeys = 8;                 // tile keys per lane in one selection round (<= 256 tiles)
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
+// Grid resistance of target i of query q (one warp): the first step at which
+// some candidate's projection dominates the target's projection, else K.
 template <int D, int SLOTS, bool RES>
-__device__ __forceinline__ void dom_warp_loop(const DomArgs &a, const uint32_t *cand, const uint32_t *tmin,
-                                              uint32_t *wsteps, long long S, long long T) {
+__device__ __forceinline__ void dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
+                                           long long T, unsigned i, uint32_t *wsteps,
+                                           unsigned long long &n_tests, unsigned long long &n_checks) {
     constexpr int WS = 32 * SLOTS;
     const int lane = threadIdx.x & 31;
-    const int K = a.K;
-    unsigned long long n_tests = 0, n_checks = 0;
-    for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(&a.hdr->work_next, 1u);
-        i = __shfl_sync(kFull, i, 0);
-        if ((long long)i >= S) break;
-        uint32_t t[D];
-        if (RES) ld_row<D>(cand, i, t); else ldg_row<D>(cand, i, t);
-        int result = K;
-        for (int w0 = 0; w0 < K; w0 += WS) {
-            const int wcount = min(WS, K - w0);
-            // this window's widths in shared memory; bounds are made on first use
+    const int K = qy.K;
+    uint32_t t[D];
+    if (RES) ld_row<D>(cand, i, t); else ldg_row<D>(cand, i, t);
+    int result = K;
+    for (int w0 = 0; w0 < K; w0 += WS) {
+        const int wcount = min(WS, K - w0);
+        // this window's widths in shared memory; bounds are made on first use
+        #pragma unroll
+        for (int j = 0; j < SLOTS; j++) {
+            const int k = w0 + 32 * j + lane;
+            wsteps[32 * j + lane] = k < K ? __ldg(qy.steps + k) : 0xFFFFFFFFu;
+        }
+        __syncwarp();
+        uint32_t U[SLOTS][D], L[SLOTS][D];
+        unsigned ready = 0;   // slots whose bounds are in U, L
+        int best = wcount;
+        // keys hold excesses >> qshift; only excesses below the window's widest width matter
+        const uint32_t wmax = wsteps[wcount - 1];
+        const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
+        for (long long tc = 0; tc < T && best > 0; tc += 32 * kTileKeys) {
+            // tile level: e_tile = max_i (tmin_i - t_i)^+ bounds every row's excess from
+            // below; a tile matters only while e_tile < delta[best - 1]. Tiles are visited in
+            // ascending order of e_tile (quantized to 24 bits for the key; exact test below).
+            uint32_t key[kTileKeys], ex[kTileKeys];
             #pragma unroll
-            for (int j = 0; j < SLOTS; j++) {
-                const int k = w0 + 32 * j + lane;
-                wsteps[32 * j + lane] = k < K ? __ldg(a.steps + k) : 0xFFFFFFFFu;
-            }
-            __syncwarp();
-            uint32_t U[SLOTS][D], L[SLOTS][D];
-            unsigned ready = 0;   // slots whose bounds are in U, L
-            int best = wcount;
-            // keys hold excesses >> qshift; only excesses below the window's widest width matter
-            const uint32_t wmax = wsteps[wcount - 1];
-            const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
-            for (long long tc = 0; tc < T && best > 0; tc += 32 * kTileKeys) {
-                // tile level: e_tile = max_i (tmin_i - t_i)^+ bounds every row's excess from
-                // below; a tile matters only while e_tile < delta[best - 1]. Tiles are visited in
-                // ascending order of e_tile (quantized to 24 bits for the key; exact test below).
-                uint32_t key[kTileKeys], ex[kTileKeys];
-                #pragma unroll
-                for (int e = 0; e < kTileKeys; e++) {
-                    key[e] = kNoTile;
-                    ex[e] = 0xFFFFFFFFu;
-                    const long long tile = tc + 32 * e + lane;
-                    if (tile < T) {
-                        uint32_t mn[D];
-                        if (RES) ld_row<D>(tmin, tile, mn); else ldg_row<D>(tmin, tile, mn);
-                        uint32_t emax = 0;
-                        bool can = false;
-                        #pragma unroll
-                        for (int q = 0; q < D; q++) {
-                            emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
-                            can |= mn[q] < t[q];
-                        }
-                        if (can && emax < wsteps[best - 1]) {
-                            ex[e] = emax;
-                            key[e] = (min(emax >> qshift, 0xFFFFFFu) << 8) | (uint32_t)(32 * e + lane);
-                        }
-                    }
-                }
-                n_checks += 32 * kTileKeys;
-                for (;;) {
-                    uint32_t lm = key[0];
-                    #pragma unroll
-                    for (int e = 1; e < kTileKeys; e++) lm = min(lm, key[e]);
-                    const uint32_t mkey = __reduce_min_sync(kFull, lm);
-                    if (mkey == kNoTile) break;
-                    const uint32_t wlim = wsteps[best - 1];
-                    if ((mkey >> 8) > min(wlim >> qshift, 0xFFFFFFu)) break;   // every tile left is too far
-                    uint32_t mine = 0xFFFFFFFFu;
-                    #pragma unroll
-                    for (int e = 0; e < kTileKeys; e++) {
-                        if (key[e] == mkey) { mine = ex[e]; key[e] = kNoTile; }
-                    }
-                    const uint32_t off = mkey & 0xFFu;
-                    const uint32_t etile = __shfl_sync(kFull, mine, off & 31u);
-                    if (etile >= wlim) continue;
-                    const long long r0 = (tc + off) * kTileRows;
-                    // candidate level: lane r looks at row r of the tile
-                    uint32_t s[D];
-                    if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
-                    uint32_t e_r = 0;
-                    bool can_r = false;
+            for (int e = 0; e < kTileKeys; e++) {
+                key[e] = kNoTile;
+                ex[e] = 0xFFFFFFFFu;
+                const long long tile = tc + 32 * e + lane;
+                if (tile < T) {
+                    uint32_t mn[D];
+                    if (RES) ld_row<D>(tmin, tile, mn); else ldg_row<D>(tmin, tile, mn);
+                    uint32_t emax = 0;
+                    bool can = false;
                     #pragma unroll
                     for (int q = 0; q < D; q++) {
-                        e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
-                        can_r |= s[q] < t[q];
+                        emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
+                        can |= mn[q] < t[q];
                     }
-                    n_checks += 32;
-                    // a row can dominate t only at widths wider than e_r; it matters only if such
-                    // a width comes before best. Rows are taken in ascending order of e_r.
-                    uint32_t ckey = (can_r && e_r < wlim) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
-                                                          : 0xFFFFFFFFu;
-                    for (;;) {
-                        const uint32_t ck = __reduce_min_sync(kFull, ckey);
-                        if (ck == 0xFFFFFFFFu) break;
-                        const int c = (int)(ck & 31u);
-                        if (lane == c) ckey = 0xFFFFFFFFu;
-                        const uint32_t ec = __shfl_sync(kFull, e_r, c);
-                        if (ec >= wsteps[best - 1]) {
-                            if ((ck >> 5) > min(wsteps[best - 1] >> qshift, 0x7FFFFFFu)) break;
-                            continue;
-                        }
-                        uint32_t sc[D];
-                        #pragma unroll
-                        for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
-                        // first slot holding a width wider than ec
-                        int jlo = 0;
-                        #pragma unroll
-                        for (int j = 0; j < SLOTS - 1; j++) jlo += (32 * j + 31 < wcount && wsteps[32 * j + 31] <= ec) ? 1 : 0;
-                        const int jhi = (best - 1) >> 5;
-                        #pragma unroll
-                        for (int j = 0; j < SLOTS; j++) {
-                            if (j < jlo || j > jhi) continue;
-                            if (!(ready & (1u << j))) {
-                                ready |= 1u << j;
-                                const int k = w0 + 32 * j + lane;
-                                const bool live = k < K;
-                                const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(a.magic) + k)
-                                                      : make_uint4(1u, 0u, 0u, 1u);
-                                const uint32_t delta = mg.w;
-                                #pragma unroll
-                                for (int q = 0; q < D; q++) {
-                                    const uint32_t v = a.dir ? ~t[q] : t[q];
-                                    const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
-                                    const uint32_t uv =
-                                        lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
-                                    U[j][q] = live ? (a.dir ? ~lv : uv) : 0u;
-                                    L[j][q] = live ? (a.dir ? ~uv : lv) : 0u;
-                                }
-                            }
-                            bool le = true, lt = false;
+                    if (can && emax < wsteps[best - 1]) {
+                        ex[e] = emax;
+                        key[e] = (min(emax >> qshift, 0xFFFFFFu) << 8) | (uint32_t)(32 * e + lane);
+                    }
+                }
+            }
+            n_checks += 32 * kTileKeys;
+            for (;;) {
+                uint32_t lm = key[0];
+                #pragma unroll
+                for (int e = 1; e < kTileKeys; e++) lm = min(lm, key[e]);
+                const uint32_t mkey = __reduce_min_sync(kFull, lm);
+                if (mkey == kNoTile) break;
+                const uint32_t wlim = wsteps[best - 1];
+                if ((mkey >> 8) > min(wlim >> qshift, 0xFFFFFFu)) break;   // every tile left is too far
+                uint32_t mine = 0xFFFFFFFFu;
+                #pragma unroll
+                for (int e = 0; e < kTileKeys; e++) {
+                    if (key[e] == mkey) { mine = ex[e]; key[e] = kNoTile; }
+                }
+                const uint32_t off = mkey & 0xFFu;
+                const uint32_t etile = __shfl_sync(kFull, mine, off & 31u);
+                if (etile >= wlim) continue;
+                const long long r0 = (tc + off) * kTileRows;
+                // candidate level: lane r looks at row r of the tile
+                uint32_t s[D];
+                if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
+                uint32_t e_r = 0;
+                bool can_r = false;
+                #pragma unroll
+                for (int q = 0; q < D; q++) {
+                    e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
+                    can_r |= s[q] < t[q];
+                }
+                n_checks += 32;
+                // a row can dominate t only at widths wider than e_r; it matters only if such
+                // a width comes before best. Rows are taken in ascending order of e_r.
+                uint32_t ckey = (can_r && e_r < wlim) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
+                                                      : 0xFFFFFFFFu;
+                for (;;) {
+                    const uint32_t ck = __reduce_min_sync(kFull, ckey);
+                    if (ck == 0xFFFFFFFFu) break;
+                    const int c = (int)(ck & 31u);
+                    if (lane == c) ckey = 0xFFFFFFFFu;
+                    const uint32_t ec = __shfl_sync(kFull, e_r, c);
+                    if (ec >= wsteps[best - 1]) {
+                        if ((ck >> 5) > min(wsteps[best - 1] >> qshift, 0x7FFFFFFu)) break;
+                        continue;
+                    }
+                    uint32_t sc[D];
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
+                    // first slot holding a width wider than ec
+                    int jlo = 0;
+                    #pragma unroll
+                    for (int j = 0; j < SLOTS - 1; j++) jlo += (32 * j + 31 < wcount && wsteps[32 * j + 31] <= ec) ? 1 : 0;
+                    const int jhi = (best - 1) >> 5;
+                    #pragma unroll
+                    for (int j = 0; j < SLOTS; j++) {
+                        if (j < jlo || j > jhi) continue;
+                        if (!(ready & (1u << j))) {
+                            ready |= 1u << j;
+                            const int k = w0 + 32 * j + lane;
+                            const bool live = k < K;
+                            const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
+                                                  : make_uint4(1u, 0u, 0u, 1u);
+                            const uint32_t delta = mg.w;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                le &= sc[q] <= U[j][q];
-                                lt |= sc[q] < L[j][q];
-                            }
-                            n_tests += 32;
-                            const unsigned msk = __ballot_sync(kFull, le & lt);
-                            if (msk) {
-                                best = min(best, 32 * j + __ffs(msk) - 1);
-                                break;
+                                const uint32_t v = qy.dir ? ~t[q] : t[q];
+                                const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
+                                const uint32_t uv =
+                                    lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+                                U[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
+                                L[j][q] = live ? (qy.dir ? ~uv : lv) : 0u;
                             }
                         }
-                        if (best == 0) break;
+                        bool le = true, lt = false;
+                        #pragma unroll
+                        for (int q = 0; q < D; q++) {
+                            le &= sc[q] <= U[j][q];
+                            lt |= sc[q] < L[j][q];
+                        }
+                        n_tests += 32;
+                        const unsigned msk = __ballot_sync(kFull, le & lt);
+                        if (msk) {
+                            best = min(best, 32 * j + __ffs(msk) - 1);
+                            break;
+                        }
                     }
                     if (best == 0) break;
                 }
+                if (best == 0) break;
             }
-            __syncwarp();
-            if (best < wcount) { result = w0 + best; break; }
         }
-        if (lane == 0) a.out[a.perm[i]] = result;
+        __syncwarp();
+        if (best < wcount) { result = w0 + best; break; }
     }
-    if (a.tests && lane == 0 && (n_tests | n_checks)) {
-        atomicAdd(a.tests, n_tests);
-        atomicAdd(a.tests + 1, n_checks);
-    }
+    if (lane == 0) qy.out[qy.perm[i]] = result;
 }
 
 template <int D, int SLOTS>
@@ -491,26 +478,112 @@ k_dominance(DomArgs a) {
     constexpr int DP = padded_dims(D);
     constexpr int WS = 32 * SLOTS;
     extern __shared__ __align__(16) uint32_t sm[];
-    const long long S = a.hdr->n_sky;
+    const long long S = *a.q.n_sky;
     if (S == 0) return;
     const long long T = (S + kTileRows - 1) / kTileRows;
     const int nwarps = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *wsteps = sm + warp * WS;
-    uint32_t *res_base = sm + nwarps * WS;
+    uint32_t *stage = sm + nwarps * WS;
     const long long cand_words = T * kTileRows * DP;
     const long long need = cand_words + T * DP;
     const bool resident = need <= (long long)a.smem_words - (long long)nwarps * WS;
     if (resident) {
         const long long n16a = cand_words / 4, n16b = (T * DP) / 4;
-        for (long long v = threadIdx.x; v < n16a; v += blockDim.x) cp_async16(res_base + 4 * v, a.cand + 4 * v);
+        for (long long v = threadIdx.x; v < n16a; v += blockDim.x) cp_async16(stage + 4 * v, a.q.cand + 4 * v);
         for (long long v = threadIdx.x; v < n16b; v += blockDim.x)
-            cp_async16(res_base + cand_words + 4 * v, a.tmin + 4 * v);
+            cp_async16(stage + cand_words + 4 * v, a.q.tmin + 4 * v);
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        dom_warp_loop<D, SLOTS, true>(a, res_base, res_base + cand_words, wsteps, S, T);
+    }
+    unsigned long long n_tests = 0, n_checks = 0;
+    if (resident) {
+        for (;;) {
+            unsigned i = 0;
+            if (lane == 0) i = atomicAdd(a.counter, 1u);
+            i = __shfl_sync(kFull, i, 0);
+            if ((long long)i >= S) break;
+            dom_target<D, SLOTS, true>(a.q, stage, stage + cand_words, T, i, wsteps, n_tests, n_checks);
+        }
     } else {
-        dom_warp_loop<D, SLOTS, false>(a, a.cand, a.tmin, wsteps, S, T);
+        for (;;) {
+            unsigned i = 0;
+            if (lane == 0) i = atomicAdd(a.counter, 1u);
+            i = __shfl_sync(kFull, i, 0);
+            if ((long long)i >= S) break;
+            dom_target<D, SLOTS, false>(a.q, a.q.cand, a.q.tmin, T, i, wsteps, n_tests, n_checks);
+        }
+    }
+    if (a.tests && lane == 0 && (n_tests | n_checks)) {
+        atomicAdd(a.tests, n_tests);
+        atomicAdd(a.tests + 1, n_checks);
+    }
+}
+
+// Many queries (same D) in one launch: work items are the (query, target)
+// pairs of all queries, handed out by one counter; candidates are read through
+// L1 (each query has its own candidate set).
+constexpr int kMaxBatch = 256;
+struct DomBatch {
+    int count;
+    unsigned *counter;        // zeroed before the launch
+    DomQuery q[kMaxBatch];
+};
+
+template <int D, int SLOTS>
+__global__ void __launch_bounds__(dom_threads<D>(), 1)
+k_dominance_batch(const __grid_constant__ DomBatch b) {
+    constexpr int WS = 32 * SLOTS;
+    __shared__ unsigned long long first[kMaxBatch + 1];   // prefix sums of the targets
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *wsteps = sm + warp * WS;
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int j = 0; j < b.count; j++) { first[j] = run; run += (unsigned long long)*b.q[j].n_sky; }
+        first[b.count] = run;
+    }
+    __syncthreads();
+    const unsigned long long total = first[b.count];
+    unsigned long long n_tests = 0, n_checks = 0;
+    for (;;) {
+        unsigned g = 0;
+        if (lane == 0) g = atomicAdd(b.counter, 1u);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= total) break;
+        int lo = 0, hi = b.count - 1;   // query j with first[j] <= g < first[j + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        const DomQuery &q = b.q[lo];
+        const long long S = *q.n_sky;
+        const long long T = (S + kTileRows - 1) / kTileRows;
+        dom_target<D, SLOTS, false>(q, q.cand, q.tmin, T, (unsigned)(g - first[lo]), wsteps, n_tests, n_checks);
+    }
+}
+
+// Division constants of K widths on the device (Granlund & Montgomery; the
+// same constants as udiv_magic): magic[4j .. 4j+3] = (m, s1, s2, delta).
+__device__ __forceinline__ uint4 magic_of(uint32_t delta) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)delta) l++;
+    const unsigned long long num = (1ull << 32) * ((1ull << l) - (unsigned long long)delta);
+    return make_uint4((uint32_t)(num / delta + 1ull), l < 1 ? (uint32_t)l : 1u, l > 1 ? (uint32_t)(l - 1) : 0u, delta);
+}
+
+constexpr int kMaxMagicJobs = 256;
+struct MagicBatch {
+    int count;
+    MagicJob j[kMaxMagicJobs];
+};
+
+__global__ void k_make_magic(const __grid_constant__ MagicBatch b) {
+    for (int jb = blockIdx.x; jb < b.count; jb += gridDim.x) {
+        const MagicJob &job = b.j[jb];
+        if (job.zero && threadIdx.x == 0) *job.zero = 0u;
+        for (int k = threadIdx.x; k < job.K; k += blockDim.x)
+            reinterpret_cast<uint4 *>(job.magic)[k] = magic_of(job.steps[k]);
     }
 }
 
@@ -553,10 +626,15 @@ cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
 }
 
 template <int D, int SLOTS>
-cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Workspace &ws,
-                          int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
+cudaError_t launch_dom_batch(const DomBatch &b, cudaStream_t st) {
+    const int smem = (dom_threads<D>() / 32) * 32 * SLOTS * 4;
+    k_dominance_batch<D, SLOTS><<<g_sm_count, dom_threads<D>(), smem, st>>>(b); note_launch();
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st) {
     const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count);
-    stage_begin(kStagePartition, st);
     const int scheme = cfg.scheme;
     PartArgs pa;
     std::memset(&pa, 0, sizeof(pa));
@@ -593,34 +671,59 @@ cudaError_t gres_stage_ds(int k, const gres_plan_cfg &cfg, int dir, int64_t n, W
     const int pb = (int)std::min<int64_t>((n + 255) / 256 + 1, (int64_t)g_sm_count * 8);
     k_permute<D><<<pb, 256, 0, st>>>(ws.sky_rows, ws.vals[0], ws.vals[1], ws.hdr,
                                      scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.perm); note_launch();
-    stage_end(kStagePartition, st);
-    DomArgs a;
-    a.cand = ws.cand;
-    a.tmin = ws.tmin;
-    a.magic = ws.magic;
-    a.steps = ws.steps;
-    a.hdr = ws.hdr;
-    a.perm = ws.perm;
-    a.out = d_step_idx;
-    a.tests = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;
-    a.K = k;
-    a.dir = dir;
-    a.smem_words = 0;
-    stage_begin(kStageDominance, st);
-    e = launch_dom<D, SLOTS>(a, st);
-    stage_end(kStageDominance, st);
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t gres_stage_d(int k, const gres_plan_cfg &cfg, int dir, int64_t n, Workspace &ws,
-                         int32_t *d_step_idx, unsigned long long *d_tests, cudaStream_t st) {
-    if (cfg.slots == 4) return gres_stage_ds<D, 4>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-    return gres_stage_ds<D, 8>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
+cudaError_t dominance_d(int slots, const DomQuery &q, unsigned *counter, unsigned long long *tests,
+                        cudaStream_t st) {
+    DomArgs a;
+    a.q = q;
+    a.counter = counter;
+    a.tests = tests;
+    a.smem_words = 0;
+    return slots == 4 ? launch_dom<D, 4>(a, st) : launch_dom<D, 8>(a, st);
 }
 
+template <int D>
+cudaError_t dominance_batch_d(int slots, const DomQuery *qs, int count, unsigned *counter, cudaStream_t st) {
+    DomBatch b;
+    b.count = count;
+    b.counter = counter;
+    for (int i = 0; i < count; i++) b.q[i] = qs[i];
+    return slots == 4 ? launch_dom_batch<D, 4>(b, st) : launch_dom_batch<D, 8>(b, st);
+}
+
+#define GRES_DISPATCH_D(d, call)                \
+    switch (d) {                                \
+        case 1: return call(1);                 \
+        case 2: return call(2);                 \
+        case 3: return call(3);                 \
+        case 4: return call(4);                 \
+        case 5: return call(5);                 \
+        case 6: return call(6);                 \
+        case 7: return call(7);                 \
+        case 8: return call(8);                 \
+        default: return cudaErrorInvalidValue;  \
+    }
+
 }  // namespace
+
+cudaError_t launch_upload_steps(uint32_t *d_steps, uint32_t *d_magic, unsigned *zero, const uint32_t *h_steps,
+                                int k, cudaStream_t st) {
+    StepChunk c;
+    for (int off = 0; off < k; off += kStepChunk) {
+        c.off = off;
+        c.count = std::min(kStepChunk, k - off);
+        for (int i = 0; i < c.count; i++) {
+            uint32_t m, s1, s2;
+            udiv_magic(h_steps[off + i], &m, &s1, &s2);
+            c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
+        }
+        k_upload_steps<<<1, 256, 0, st>>>(c, d_steps, d_magic, nullptr, 0, off == 0 ? zero : nullptr); note_launch();
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st) {
     StepChunk c;
@@ -632,7 +735,47 @@ cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps,
             udiv_magic(h_steps[off + i], &m, &s1, &s2);
             c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
         }
-        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic, off == 0 ? ws.hdr : nullptr, (long long)n); note_launch();
+        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic, off == 0 ? ws.hdr : nullptr, (long long)n,
+                                          nullptr); note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+#define GRES_PART(D) partition_d<D>(cfg, n, ws, st)
+    GRES_DISPATCH_D(d, GRES_PART)
+#undef GRES_PART
+}
+
+cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,
+                             unsigned long long *tests, cudaStream_t st) {
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+#define GRES_DOM(D) dominance_d<D>(slots, q, counter, tests, st)
+    GRES_DISPATCH_D(d, GRES_DOM)
+#undef GRES_DOM
+}
+
+cudaError_t launch_dominance_batch(int d, int slots, const DomQuery *qs, int count, unsigned *counter,
+                                   cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (count > kMaxBatch) return cudaErrorInvalidValue;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+#define GRES_DOMB(D) dominance_batch_d<D>(slots, qs, count, counter, st)
+    GRES_DISPATCH_D(d, GRES_DOMB)
+#undef GRES_DOMB
+}
+
+cudaError_t launch_make_magic(const MagicJob *jobs, int count, cudaStream_t st) {
+    for (int off = 0; off < count; off += kMaxMagicJobs) {
+        MagicBatch b;
+        b.count = std::min(kMaxMagicJobs, count - off);
+        for (int i = 0; i < b.count; i++) b.j[i] = jobs[off + i];
+        k_make_magic<<<b.count, 256, 0, st>>>(b); note_launch();
     }
     return cudaGetLastError();
 }
@@ -642,19 +785,25 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
                               const int64_t * /*d_sky_idx*/, int32_t *d_step_idx,
                               unsigned long long *d_tests, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    cudaError_t e = device_props();
+    stage_begin(kStagePartition, st);
+    cudaError_t e = launch_partition(d, cfg, n, ws, st);
+    stage_end(kStagePartition, st);
     if (e != cudaSuccess) return e;
-    switch (d) {
-        case 1: return gres_stage_d<1>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 2: return gres_stage_d<2>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 3: return gres_stage_d<3>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 4: return gres_stage_d<4>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 5: return gres_stage_d<5>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 6: return gres_stage_d<6>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 7: return gres_stage_d<7>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        case 8: return gres_stage_d<8>(k, cfg, dir, n, ws, d_step_idx, d_tests, st);
-        default: return cudaErrorInvalidValue;
-    }
+    DomQuery q;
+    q.cand = ws.cand;
+    q.tmin = ws.tmin;
+    q.perm = ws.perm;
+    q.n_sky = &ws.hdr->n_sky;
+    q.magic = ws.magic;
+    q.steps = ws.steps;
+    q.out = d_step_idx;
+    q.K = k;
+    q.dir = dir;
+    stage_begin(kStageDominance, st);
+    e = launch_dominance(d, cfg.slots, q, &ws.hdr->work_next,
+                         (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr, st);
+    stage_end(kStageDominance, st);
+    return e;
 }
 
 cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps, int k,

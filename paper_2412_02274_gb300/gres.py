@@ -46,6 +46,13 @@ class PlanCfg(ctypes.Structure):
                 ("reps", _i32), ("slots", _i32), ("flags", _i32), ("reserved", _i32)]
 
 
+class Instance(ctypes.Structure):
+    """``gres_instance``: one problem of a gres_batch call (device pointers)."""
+    _fields_ = [("d_data", _p), ("n", _i64), ("d", _i32), ("dir", _i32), ("d_steps", _p),
+                ("k", _i32), ("cfg", PlanCfg), ("d_sky_idx", _p), ("d_step_idx", _p),
+                ("d_sky_count", _p)]
+
+
 def plan(scheme: int = PART_GRID, m: int = 0, p: int = 0, slice_dim: int = 0, reps: int = 0,
          slots: int = 0, count_tests: bool = False) -> PlanCfg:
     return PlanCfg(scheme, m, p, slice_dim, reps, slots, FLAG_COUNT_TESTS if count_tests else 0, 0)
@@ -79,9 +86,22 @@ def load():
         lib.gres_launch_count.argtypes = []
         lib.gres_timing_enable.argtypes = [_i32]
         lib.gres_timing_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]
+        lib.gres_dataset_create.argtypes = [_p, _i64, _i32, _i32, ctypes.POINTER(PlanCfg), _i32, _p,
+                                            ctypes.POINTER(_p)]
+        lib.gres_dataset_destroy.argtypes = [_p]
+        lib.gres_dataset_info.argtypes = [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                          ctypes.POINTER(_i64), ctypes.POINTER(_size)]
+        lib.gres_dataset_sky_idx.argtypes = [_p, _p, _i32, _p]
+        lib.gres_query_workspace_size.argtypes = [_i32, ctypes.POINTER(_size)]
+        lib.gres_query.argtypes = [_p, _p, _i32, _p, _size, _p, _p]
+        lib.gres_batch_workspace_size.argtypes = [ctypes.POINTER(Instance), _i32, ctypes.POINTER(_size)]
+        lib.gres_batch.argtypes = [ctypes.POINTER(Instance), _i32, _p, _size, _p]
         for name in ("gres_workspace_size", "gres_workspace_size_host", "sky_compute",
                      "gres_compute", "gres_compute_host", "gres_gproj", "gres_udiv_magic",
-                     "gres_timing_enable", "gres_timing_read"):
+                     "gres_timing_enable", "gres_timing_read", "gres_dataset_create",
+                     "gres_dataset_destroy", "gres_dataset_info", "gres_dataset_sky_idx",
+                     "gres_query_workspace_size", "gres_query", "gres_batch_workspace_size",
+                     "gres_batch"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -260,3 +280,93 @@ def gproj(values, steps, stream=None):
     _check(load().gres_gproj(_ptr(v), count, st.ctypes.data_as(ctypes.c_void_p), len(st),
                              _ptr(out), _stream_ptr(stream)))
     return out[:, :count]
+
+
+# ---- resident datasets and queries ---------------------------------------------------
+
+class Dataset:
+    """A prepared dataset (skyline + candidate tiles on the device) for repeated queries."""
+
+    def __init__(self, data, direction: int = MIN, cfg: PlanCfg | None = None, stream=None):
+        import torch
+        self._lib = load()
+        h = _p()
+        cfgp = ctypes.byref(cfg) if cfg is not None else None
+        if isinstance(data, np.ndarray):
+            a = np.ascontiguousarray(data, dtype=np.uint32)
+            n, d = a.shape
+            ptr, on_host = a.ctypes.data_as(ctypes.c_void_p), 1
+        else:
+            a = data
+            n, d = int(a.shape[0]), int(a.shape[1])
+            ptr, on_host = _ptr(a), 0 if a.is_cuda else 1
+        _check(self._lib.gres_dataset_create(ptr, int(n), int(d), int(direction), cfgp, on_host,
+                                             _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        nn, dd, ss, bb = _i64(0), _i32(0), _i64(0), _size(0)
+        _check(self._lib.gres_dataset_info(h, ctypes.byref(nn), ctypes.byref(dd), ctypes.byref(ss),
+                                           ctypes.byref(bb)))
+        self.n, self.d, self.S, self.device_bytes = nn.value, dd.value, ss.value, bb.value
+        self._torch = torch
+
+    def sky_idx(self, stream=None):
+        out = np.empty(max(self.S, 1), dtype=np.int64)
+        _check(self._lib.gres_dataset_sky_idx(self._h, out.ctypes.data_as(ctypes.c_void_p), 1,
+                                              _stream_ptr(stream)))
+        return out[: self.S]
+
+    def query(self, steps, out=None, qws=None, stream=None):
+        """Step index per skyline row (CUDA int32 tensor of S entries), queued on `stream`."""
+        torch = self._torch
+        st = _steps_array(steps)
+        k = len(st)
+        if qws is None:
+            sz = _size(0)
+            _check(self._lib.gres_query_workspace_size(k, ctypes.byref(sz)))
+            qws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        if out is None:
+            out = torch.empty(max(self.S, 1), dtype=torch.int32, device="cuda")
+        _check(self._lib.gres_query(self._h, st.ctypes.data_as(ctypes.c_void_p), k, _ptr(qws),
+                                    qws.numel(), _ptr(out), _stream_ptr(stream)))
+        return out[: self.S]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.gres_dataset_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch(problems, stream=None, ws=None):
+    """Many gres_compute problems in one gres_batch call.
+
+    ``problems``: list of dicts with ``data`` ((n, d) int32 CUDA tensor), ``steps``
+    (1-D int32 CUDA tensor of widths), optional ``direction`` and ``cfg``. Returns the
+    per-instance output tensors ``(sky_idx, step_idx, sky_count)`` (full capacity, with
+    S on the device) and the ctypes instance array (keep both alive while replaying a
+    captured graph)."""
+    torch = _torch()
+    insts = (Instance * max(len(problems), 1))()
+    outs = []
+    for i, pr in enumerate(problems):
+        x = pr["data"]
+        n, d = int(x.shape[0]), int(x.shape[1])
+        st = pr["steps"]
+        sky = torch.empty(max(n, 1), dtype=torch.int64, device=x.device)
+        res = torch.empty(max(n, 1), dtype=torch.int32, device=x.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=x.device)
+        cfg = pr.get("cfg") or PlanCfg()
+        insts[i] = Instance(x.data_ptr(), n, d, int(pr.get("direction", MIN)), st.data_ptr(), int(st.numel()),
+                            cfg, sky.data_ptr(), res.data_ptr(), cnt.data_ptr())
+        outs.append((sky, res, cnt))
+    if ws is None:
+        sz = _size(0)
+        _check(load().gres_batch_workspace_size(insts, len(problems), ctypes.byref(sz)))
+        ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+    _check(load().gres_batch(insts, len(problems), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return outs, insts, ws
