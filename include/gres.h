@@ -216,6 +216,60 @@ typedef struct {
 gres_status gres_batch_workspace_size(const gres_instance *inst, int32_t n_inst, size_t *bytes);
 gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, size_t ws_bytes, void *stream);
 
+/* ---- serving: resident datasets, continuous batching -------------------------
+ * A server keeps prepared datasets in device memory within an HBM budget and
+ * answers gres queries (a dataset and a step list) submitted from any thread.
+ * A scheduler thread keeps up to max_inflight batches on the GPU; whenever a
+ * slot frees up it takes up to max_batch queued queries (arrival order) and
+ * runs them as one batch: one copy of their widths, one kernel for their
+ * division constants, one grid-dominance launch per dimensionality over all
+ * their targets, one copy of the results. Queries that arrive while batches
+ * run are admitted as slots free up. Results are identical to gres_query /
+ * gres_compute (the kernels are deterministic per target). */
+typedef struct gres_server gres_server;
+typedef struct {
+    int32_t max_batch;       /* queries per batch, 1..256 (0: 64)                   */
+    int32_t max_inflight;    /* batches on the GPU at once, 1..16 (0: 2)            */
+    int32_t queue_capacity;  /* queued queries before GRES_EAGAIN (0: 65536)        */
+    int32_t max_k;           /* longest step list accepted (0: 4096)                */
+    int32_t start_paused;    /* nonzero: queue queries but start no batch until
+                                gres_serve_resume (admission control, tests)        */
+} gres_serve_cfg;
+
+/* Creates a server on the current device. hbm_budget_bytes bounds the device
+ * memory it holds (datasets and batch buffers); GRES_ENOMEM if it cannot even
+ * hold the batch buffers. cfg may be NULL. */
+gres_status gres_serve_create(size_t hbm_budget_bytes, const gres_serve_cfg *cfg, gres_server **out);
+/* Prepares and keeps a dataset (as gres_dataset_create); *out_id names it.
+ * GRES_ENOMEM (and nothing kept) if it would exceed the budget. */
+gres_status gres_serve_add_dataset(gres_server *sv, const uint32_t *data, int64_t n, int32_t d, int32_t dir,
+                                   const gres_plan_cfg *plan, int32_t data_on_host, int32_t *out_id);
+/* Drops a dataset; GRES_EAGAIN while queries on it are unfinished. */
+gres_status gres_serve_remove_dataset(gres_server *sv, int32_t id);
+/* Queues a query (widths copied; host, k, strictly ascending, >= 1, k <=
+ * max_k). GRES_EAGAIN if the queue is full. */
+gres_status gres_serve_submit(gres_server *sv, int32_t dataset_id, const uint32_t *h_steps, int32_t k,
+                              uint64_t *out_ticket);
+/* Waits up to timeout_us (0: do not wait; < 0: no limit) for a query; then
+ * writes its S results (skyline order of the dataset) to h_step_idx (capacity
+ * cap), S to h_sky_count and the submit-to-completion time to h_latency_ns
+ * (either may be NULL), and forgets the ticket. GRES_EAGAIN if it is not
+ * finished in time (the ticket stays valid). */
+gres_status gres_serve_poll(gres_server *sv, uint64_t ticket, int32_t *h_step_idx, int64_t cap,
+                            int64_t *h_sky_count, int64_t *h_latency_ns, int64_t timeout_us);
+/* Starts batches again after start_paused (or gres_serve_pause). */
+gres_status gres_serve_resume(gres_server *sv);
+/* Stops starting new batches (running ones finish; queries keep queueing). */
+gres_status gres_serve_pause(gres_server *sv);
+/* Withdraws a query: dropped if still queued, results discarded if running. */
+gres_status gres_serve_cancel(gres_server *sv, uint64_t ticket);
+/* Batches run, queries answered, kernels launched, device bytes held. */
+gres_status gres_serve_stats(gres_server *sv, uint64_t *batches, uint64_t *queries, uint64_t *launches,
+                             size_t *device_bytes);
+/* Stops the scheduler (queued queries are dropped, running batches finish)
+ * and frees everything the server holds. */
+gres_status gres_serve_destroy(gres_server *sv);
+
 /* Grid projection (Sec. 2) of `count` values at each of k widths:
  * d_out[j*count + i] = floor(d_values[i] / h_steps[j]) (the paper's
  * floor(t[i] g) numerator with delta = 2^B / g). Division by a run-time

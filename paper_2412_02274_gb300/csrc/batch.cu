@@ -105,23 +105,6 @@ gres_status normalize_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *o
 
 }  // namespace
 
-// A prepared dataset: the skyline and the candidate tiles, on the device.
-struct gres_dataset {
-    int device;
-    int64_t n;
-    int32_t d;
-    int32_t dir;
-    int32_t slots;
-    int64_t S;
-    void *mem;            // one allocation holding everything below
-    size_t bytes;
-    int64_t *sky_idx;     // S: skyline rows, ascending
-    uint32_t *perm;       // S: partition position -> skyline position
-    uint32_t *cand;       // T*32 rows of DP words (partition order, sentinel-padded)
-    uint32_t *tmin;       // T rows of DP words
-    long long *n_sky;     // S on the device
-};
-
 extern "C" {
 
 gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int32_t dir,

@@ -238,3 +238,21 @@ cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t
                          uint32_t *d_out, cudaStream_t st);
 
 }  // namespace gres
+
+// A prepared dataset: the skyline and the candidate tiles, on the device
+// (gres_dataset_create). One device allocation holds every array.
+struct gres_dataset {
+    int device;
+    int64_t n;
+    int32_t d;
+    int32_t dir;
+    int32_t slots;
+    int64_t S;
+    void *mem;
+    size_t bytes;
+    int64_t *sky_idx;     // S: skyline rows, ascending
+    uint32_t *perm;       // S: partition position -> skyline position
+    uint32_t *cand;       // T*32 rows of DP words (partition order, sentinel-padded)
+    uint32_t *tmin;       // T rows of DP words
+    long long *n_sky;     // S on the device
+};

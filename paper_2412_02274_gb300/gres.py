@@ -46,6 +46,12 @@ class PlanCfg(ctypes.Structure):
                 ("reps", _i32), ("slots", _i32), ("flags", _i32), ("reserved", _i32)]
 
 
+class ServeCfg(ctypes.Structure):
+    """``gres_serve_cfg``."""
+    _fields_ = [("max_batch", _i32), ("max_inflight", _i32), ("queue_capacity", _i32), ("max_k", _i32),
+                ("start_paused", _i32)]
+
+
 class Instance(ctypes.Structure):
     """``gres_instance``: one problem of a gres_batch call (device pointers)."""
     _fields_ = [("d_data", _p), ("n", _i64), ("d", _i32), ("dir", _i32), ("d_steps", _p),
@@ -96,6 +102,23 @@ def load():
         lib.gres_query.argtypes = [_p, _p, _i32, _p, _size, _p, _p]
         lib.gres_batch_workspace_size.argtypes = [ctypes.POINTER(Instance), _i32, ctypes.POINTER(_size)]
         lib.gres_batch.argtypes = [ctypes.POINTER(Instance), _i32, _p, _size, _p]
+        lib.gres_serve_create.argtypes = [_size, ctypes.POINTER(ServeCfg), ctypes.POINTER(_p)]
+        lib.gres_serve_add_dataset.argtypes = [_p, _p, _i64, _i32, _i32, ctypes.POINTER(PlanCfg), _i32,
+                                               ctypes.POINTER(_i32)]
+        lib.gres_serve_remove_dataset.argtypes = [_p, _i32]
+        lib.gres_serve_submit.argtypes = [_p, _i32, _p, _i32, ctypes.POINTER(ctypes.c_uint64)]
+        lib.gres_serve_poll.argtypes = [_p, ctypes.c_uint64, _p, _i64, ctypes.POINTER(_i64),
+                                        ctypes.POINTER(_i64), _i64]
+        lib.gres_serve_cancel.argtypes = [_p, ctypes.c_uint64]
+        lib.gres_serve_resume.argtypes = [_p]
+        lib.gres_serve_pause.argtypes = [_p]
+        lib.gres_serve_stats.argtypes = [_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_size)]
+        lib.gres_serve_destroy.argtypes = [_p]
+        for name in ("gres_serve_create", "gres_serve_add_dataset", "gres_serve_remove_dataset",
+                     "gres_serve_submit", "gres_serve_poll", "gres_serve_cancel", "gres_serve_resume",
+                     "gres_serve_pause", "gres_serve_stats", "gres_serve_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("gres_workspace_size", "gres_workspace_size_host", "sky_compute",
                      "gres_compute", "gres_compute_host", "gres_gproj", "gres_udiv_magic",
                      "gres_timing_enable", "gres_timing_read", "gres_dataset_create",
@@ -370,3 +393,75 @@ def batch(problems, stream=None, ws=None):
         ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
     _check(load().gres_batch(insts, len(problems), _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return outs, insts, ws
+
+
+# ---- serving --------------------------------------------------------------------------
+
+class Server:
+    """A gres query server (resident datasets, continuous batching) on the current GPU."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch: int = 0, max_inflight: int = 0,
+                 queue_capacity: int = 0, max_k: int = 0, start_paused: bool = False):
+        _torch()
+        self._lib = load()
+        h = _p()
+        cfg = ServeCfg(max_batch, max_inflight, queue_capacity, max_k, 1 if start_paused else 0)
+        _check(self._lib.gres_serve_create(int(hbm_budget_bytes), ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.S = {}
+
+    def add_dataset(self, data, direction: int = MIN, cfg: PlanCfg | None = None) -> int:
+        a = np.ascontiguousarray(np.asarray(data, dtype=np.uint32))
+        n, d = a.shape
+        out = _i32(0)
+        cfgp = ctypes.byref(cfg) if cfg is not None else None
+        _check(self._lib.gres_serve_add_dataset(self._h, a.ctypes.data_as(ctypes.c_void_p), int(n), int(d),
+                                                int(direction), cfgp, 1, ctypes.byref(out)))
+        return int(out.value)
+
+    def remove_dataset(self, dataset_id: int) -> None:
+        _check(self._lib.gres_serve_remove_dataset(self._h, int(dataset_id)))
+
+    def submit(self, dataset_id: int, steps) -> int:
+        st = _steps_array(steps)
+        t = ctypes.c_uint64(0)
+        _check(self._lib.gres_serve_submit(self._h, int(dataset_id), st.ctypes.data_as(ctypes.c_void_p),
+                                           len(st), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_us: int = -1, cap: int = 1 << 22):
+        """(step_idx numpy int32, latency_ns), or None if not finished within the timeout."""
+        out = np.empty(cap, dtype=np.int32)
+        S, lat = _i64(0), _i64(0)
+        rc = self._lib.gres_serve_poll(self._h, ctypes.c_uint64(ticket), out.ctypes.data_as(ctypes.c_void_p),
+                                       cap, ctypes.byref(S), ctypes.byref(lat), int(timeout_us))
+        if rc == 3:
+            return None
+        _check(rc)
+        return out[: S.value].copy(), int(lat.value)
+
+    def cancel(self, ticket: int) -> None:
+        _check(self._lib.gres_serve_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def resume(self) -> None:
+        _check(self._lib.gres_serve_resume(self._h))
+
+    def pause(self) -> None:
+        _check(self._lib.gres_serve_pause(self._h))
+
+    def stats(self) -> dict:
+        b, q, l, m = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0), _size(0)
+        _check(self._lib.gres_serve_stats(self._h, ctypes.byref(b), ctypes.byref(q), ctypes.byref(l),
+                                          ctypes.byref(m)))
+        return {"batches": b.value, "queries": q.value, "launches": l.value, "device_bytes": m.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _check(self._lib.gres_serve_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -101,3 +101,18 @@ def test_division_constants_full_range_samples():
         np.testing.assert_array_equal(_apply_magic(vv, m, s1, s2), vv // np.uint64(delta))
     with pytest.raises(G.GresError):
         G.udiv_magic(0)
+
+
+def test_server_argument_checks_need_no_gpu():
+    lib = G.load()
+    out = ctypes.c_void_p()
+    assert lib.gres_serve_create(1 << 30, None, None) == 1
+    bad = G.ServeCfg(0, 99, 0, 0, 0)                      # max_inflight out of range
+    assert lib.gres_serve_create(1 << 30, ctypes.byref(bad), ctypes.byref(out)) == 1
+    bad = G.ServeCfg(1000, 0, 0, 0, 0)                    # max_batch out of range
+    assert lib.gres_serve_create(1 << 30, ctypes.byref(bad), ctypes.byref(out)) == 1
+    t = ctypes.c_uint64(0)
+    steps = np.array([1, 2], np.uint32)
+    assert lib.gres_serve_submit(None, 0, steps.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(t)) == 1
+    assert lib.gres_serve_poll(None, 1, None, 0, None, None, 0) == 1
+    assert lib.gres_serve_destroy(None) == 0
