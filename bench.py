@@ -48,6 +48,7 @@ WORKLOADS = {
     "uni-n1000-d2-b16-k64-grid": ("uni", 1_000, 2, 16, ("lin", 64, 64), "grid", 0, 0),
 }
 DEFAULT_WORKLOAD = "ant-n100000-d4-b20-k256-grid-m4"
+MULTI_WORKLOADS = ("batch-512", "serve-10k")
 SCHEMES = {"none": 0, "grid": 1, "angular": 2, "sliced": 3}
 METRIC = "effective grid-dominance tests/s (skyline + gres of every skyline tuple)"
 UNIT = "tests/s"
@@ -383,13 +384,190 @@ def run_ours(args):
     return 0
 
 
+# ---- many instances (one gres_batch per step) ------------------------------------
+def batch_problems(count=512, seed=0):
+    """512 instances: N log-uniform in [1e3, 2e5], d in {2..8}, UNI / ANT (0.05) /
+    CLU (16 clusters, 0.02), values in [0, 2^20), 128 log-spaced widths."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(1e3), np.log(2e5)))))
+        d = int(rng.integers(2, 9))
+        dist = ("uni", "ant", "clu")[int(rng.integers(0, 3))]
+        out.append((dist, n, d, make_dataset(dist, n, d, bits=20, seed=seed * 100000 + i)))
+    return out, steps_log(128, 16)
+
+
+def run_batch(args):
+    import torch
+    from paper_2412_02274_gb300 import gres as G
+    dev = torch.device("cuda", torch.cuda.current_device())
+    insts, steps = batch_problems()
+    K = len(steps)
+    tsteps = torch.from_numpy(steps.view(np.int32)).to(dev)
+    probs = [{"data": G.to_device_u32(data, dev), "steps": tsteps, "cfg": G.plan(G.PART_GRID)}
+             for _, _, _, data in insts]
+    stream = torch.cuda.current_stream(dev)
+    outs, cinsts, ws = G.batch(probs, stream=stream)
+    torch.cuda.synchronize(dev)
+    eff = 0
+    for sky, res, cnt in outs:
+        S = int(cnt.item())
+        eff += effective_tests(res[:S].cpu().numpy(), K)
+    lib = G.load()
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(stream)
+    c0 = G.launch_count()
+    with torch.cuda.graph(graph, stream=cap):
+        G._check(lib.gres_batch(cinsts, len(probs), G._ptr(ws), ws.numel(), G._stream_ptr(cap)))
+    per_call = G.launch_count() - c0
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    t_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_ms.append(a.elapsed_time(b))
+    clocks = sampler.stop()
+    ms = float(np.mean(t_ms))
+    # the same 512 problems one at a time (one gres_compute per instance, direct calls)
+    wss = {}
+    for _ in range(max(1, args.warmup // 2)):
+        for pr in probs:
+            n, d = pr["data"].shape
+            key = (int(n), int(d))
+            if key not in wss:
+                wss[key] = G.alloc_workspace(int(n), int(d), K)
+            G.gres_compute(pr["data"], steps, G.MIN, pr["cfg"], ws=wss[key], sync=False, stream=stream)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for pr in probs:
+        n, d = pr["data"].shape
+        G.gres_compute(pr["data"], steps, G.MIN, pr["cfg"], ws=wss[(int(n), int(d))], sync=False,
+                       stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_single = a.elapsed_time(b)
+    line = {"metric": "gres instances/s (512 uneven instances per step)", "value": len(probs) / (ms / 1e3),
+            "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batch-512", "instances": len(probs), "widths": K,
+                       "n_range": [1000, 200000], "d_range": [2, 8], "distributions": ["uni", "ant", "clu"],
+                       "launch": "one gres_batch captured in a CUDA graph",
+                       "l2": "256 MiB write between timed steps"},
+            "effective_tests_per_s": eff / (ms / 1e3),
+            "one_at_a_time": {"ms": ms_single, "instances_per_s": len(probs) / (ms_single / 1e3),
+                              "speedup_of_batch": ms_single / ms},
+            "gpu_launches": per_call * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- serving ----------------------------------------------------------------------
+def serve_datasets(count=64, seed=1):
+    """64 datasets: N log-uniform in [1e3, 2e6], d in {2..8}, UNI / ANT / CLU mix."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(1e3), np.log(2e6)))))
+        d = int(rng.integers(2, 9))
+        dist = ("uni", "ant", "clu")[i % 3]
+        out.append(make_dataset(dist, n, d, bits=20, seed=seed * 100000 + i))
+    return out
+
+
+def run_serve(args):
+    import torch
+    from paper_2412_02274_gb300 import gres as G
+    rng = np.random.default_rng(2)
+    datas = serve_datasets()
+    sv = G.Server(64 << 30, max_batch=128, max_inflight=3)
+    ids = [sv.add_dataset(x, G.MIN, G.plan(G.PART_GRID)) for x in datas]
+    nq = 10000
+    qs = [(ids[int(rng.integers(0, len(ids)))], steps_log(int(rng.integers(64, 257)), 16)) for _ in range(nq)]
+    # warm-up
+    for t in [sv.submit(i, st) for i, st in qs[:200]]:
+        sv.poll(t)
+    # saturation: every query at once
+    t0 = time.perf_counter()
+    tickets = [sv.submit(i, st) for i, st in qs]
+    lats = [sv.poll(t)[1] for t in tickets]
+    sat_s = time.perf_counter() - t0
+    sat_qps = nq / sat_s
+    # Poisson arrivals at 80 % of the saturating rate
+    lam = 0.8 * sat_qps
+    gaps = rng.exponential(1.0 / lam, size=nq)
+    done = []
+
+    def poller(ts):
+        for t in ts:
+            done.append(sv.poll(t)[1])
+
+    tickets = []
+    t0 = time.perf_counter()
+    nxt = t0
+    for (i, st), g in zip(qs, gaps):
+        nxt += g
+        while time.perf_counter() < nxt:
+            pass
+        tickets.append(sv.submit(i, st))
+    for t in tickets:
+        done.append(sv.poll(t)[1])
+    load_s = time.perf_counter() - t0
+    lat = np.array(done) / 1e6
+    stats = sv.stats()
+    # one query at a time: each query alone, waiting for it before the next
+    alone = [G.Dataset(x, G.MIN, G.plan(G.PART_GRID)) for x in datas]
+    stream = torch.cuda.current_stream()
+    qws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    outb = torch.empty(1 << 21, dtype=torch.int32, device="cuda")
+    for i, st in qs[:100]:
+        alone[i].query(st, out=outb, qws=qws, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = []
+    for i, st in qs[:2000]:
+        a = time.perf_counter()
+        r = alone[i].query(st, out=outb, qws=qws, stream=stream)
+        r.cpu()
+        single.append(time.perf_counter() - a)
+    single_qps = 2000 / (time.perf_counter() - t0)
+    sv.close()
+    line = {"metric": "gres queries/s served (10,000 queries on 64 resident datasets)", "value": sat_qps,
+            "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": sat_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "serve-10k", "datasets": len(datas), "n_range": [1000, 2000000],
+                       "d_range": [2, 8], "widths": [64, 256], "max_batch": 128, "max_inflight": 3},
+            "saturation": {"qps": sat_qps, "p50_ms": float(np.percentile(lats, 50)) / 1e6,
+                           "p99_ms": float(np.percentile(lats, 99)) / 1e6},
+            "poisson_80pct": {"lambda_qps": lam, "achieved_qps": nq / load_s,
+                              "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
+            "one_at_a_time": {"qps": single_qps, "p50_ms": 1e3 * float(np.percentile(single, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(single, 99))},
+            "server": stats}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(MULTI_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", action=argparse.BooleanOptionalAction, default=True,
                     help="each step replays a gres_compute captured in a CUDA graph "
@@ -401,6 +579,10 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch-512":
+        return run_batch(args)
+    if args.workload == "serve-10k":
+        return run_serve(args)
     return run_ours(args)
 
 

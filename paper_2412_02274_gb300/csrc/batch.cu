@@ -149,7 +149,9 @@ gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int3
     const size_t b_perm = align256(4 * (size_t)(S > 0 ? S : 1));
     const size_t b_cand = align256(4 * (size_t)DP * (size_t)(T > 0 ? T : 1) * gres::kTileRows);
     const size_t b_tmin = align256(4 * (size_t)DP * (size_t)(T > 0 ? T : 1));
-    const size_t bytes = b_sky + b_perm + b_cand + b_tmin + 256;
+    const int64_t T2 = (T + 31) / 32;
+    const size_t b_smin = align256(4 * (size_t)DP * (size_t)(T2 > 0 ? T2 : 1));
+    const size_t bytes = b_sky + b_perm + b_cand + b_tmin + b_smin + 256;
     void *mem = nullptr;
     e = cudaMalloc(&mem, bytes);
     if (e != cudaSuccess) {
@@ -172,7 +174,8 @@ gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int3
     ds->perm = reinterpret_cast<uint32_t *>(m + b_sky);
     ds->cand = reinterpret_cast<uint32_t *>(m + b_sky + b_perm);
     ds->tmin = reinterpret_cast<uint32_t *>(m + b_sky + b_perm + b_cand);
-    ds->n_sky = reinterpret_cast<long long *>(m + b_sky + b_perm + b_cand + b_tmin);
+    ds->smin = reinterpret_cast<uint32_t *>(m + b_sky + b_perm + b_cand + b_tmin);
+    ds->n_sky = reinterpret_cast<long long *>(m + b_sky + b_perm + b_cand + b_tmin + b_smin);
     e = cudaMemcpyAsync(ds->n_sky, &ws.hdr->n_sky, sizeof(long long), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && S > 0) {
         e = cudaMemcpyAsync(ds->sky_idx, tmp_sky, 8 * (size_t)S, cudaMemcpyDeviceToDevice, st);
@@ -181,6 +184,8 @@ gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int3
             e = cudaMemcpyAsync(ds->cand, ws.cand, 4 * (size_t)DP * T * gres::kTileRows, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ds->tmin, ws.tmin, 4 * (size_t)DP * T, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ds->smin, ws.smin, 4 * (size_t)DP * T2, cudaMemcpyDeviceToDevice, st);
     }
     cudaFreeAsync(tmp, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -255,6 +260,7 @@ gres_status gres_query(const gres_dataset *ds, const uint32_t *h_steps, int32_t 
     gres::DomQuery dq;
     dq.cand = ds->cand;
     dq.tmin = ds->tmin;
+    dq.smin = ds->smin;
     dq.perm = ds->perm;
     dq.n_sky = ds->n_sky;
     dq.magic = magic;
@@ -365,6 +371,7 @@ gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, si
                 gres::DomQuery q;
                 q.cand = ws[(size_t)i].cand;
                 q.tmin = ws[(size_t)i].tmin;
+                q.smin = ws[(size_t)i].smin;
                 q.perm = ws[(size_t)i].perm;
                 q.n_sky = &ws[(size_t)i].hdr->n_sky;
                 q.magic = ws[(size_t)i].magic;

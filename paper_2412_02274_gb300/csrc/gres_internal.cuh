@@ -193,6 +193,7 @@ void stage_end(int stage, cudaStream_t st);
 struct DomQuery {
     const uint32_t *cand;     // T*32 rows, DP words each (partition order, sentinel-padded)
     const uint32_t *tmin;     // T rows, DP words each
+    const uint32_t *smin;     // ceil(T / 32) super-tile rows, DP words each
     const uint32_t *perm;     // partition position -> skyline position
     const long long *n_sky;   // S (device)
     const uint32_t *magic;    // K * 4: (m, s1, s2, delta)
@@ -254,5 +255,6 @@ struct gres_dataset {
     uint32_t *perm;       // S: partition position -> skyline position
     uint32_t *cand;       // T*32 rows of DP words (partition order, sentinel-padded)
     uint32_t *tmin;       // T rows of DP words
+    uint32_t *smin;       // ceil(T / 32) rows of DP words
     long long *n_sky;     // S on the device
 };

@@ -260,47 +260,59 @@ __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
 }
 
 // Candidate rows in partition order, padded to whole 32-row tiles with
-// sentinel rows (all ones: never dominate), and each tile's per-attribute
-// minimum. One warp per tile.
+// sentinel rows (all ones: never dominate), each tile's per-attribute minimum
+// (tmin) and each 1024-row super-tile's minimum (smin). One block of 1024
+// threads per super-tile; warp w builds tile w of it.
 template <int D>
-__global__ void k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1,
-                          const WsHeader *h, int identity, uint32_t *cand, uint32_t *tmin,
-                          uint32_t *perm) {
+__global__ void __launch_bounds__(1024)
+k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1,
+          const WsHeader *h, int identity, uint32_t *cand, uint32_t *tmin, uint32_t *smin,
+          uint32_t *perm) {
     constexpr int DP = padded_dims(D);
     const long long S = h->n_sky;
     const long long T = (S + kTileRows - 1) / kTileRows;
+    const long long T2 = (T + 31) / 32;
+    if ((long long)blockIdx.x >= T2) return;
     const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    const int lane = threadIdx.x & 31;
-    const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long tile = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < T; tile += wstride) {
-        const long long i = tile * kTileRows + lane;
-        uint32_t x[DP];
-        if (i < S) {
-            const uint32_t j = identity ? (uint32_t)i : vals[i];
-            perm[i] = j;
-            const uint4 *p = reinterpret_cast<const uint4 *>(sky_rows + (long long)j * DP);
-            uint4 a = p[0];
-            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-            if (DP == 8) { uint4 b = p[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
-        } else {
-            #pragma unroll
-            for (int q = 0; q < DP; q++) x[q] = kSentinel;
-        }
+    __shared__ uint32_t wm[32][DP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long tile = (long long)blockIdx.x * 32 + w;
+    const long long i = tile * kTileRows + lane;
+    uint32_t x[DP];
+    if (i < S) {
+        const uint32_t j = identity ? (uint32_t)i : vals[i];
+        perm[i] = j;
+        const uint4 *p = reinterpret_cast<const uint4 *>(sky_rows + (long long)j * DP);
+        uint4 a = p[0];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        if (DP == 8) { uint4 b = p[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
+    } else {
+        #pragma unroll
+        for (int q = 0; q < DP; q++) x[q] = kSentinel;
+    }
+    if (tile < T) {
         uint4 *dst = reinterpret_cast<uint4 *>(cand + i * DP);
         dst[0] = make_uint4(x[0], x[1], x[2], x[3]);
         if (DP == 8) dst[1] = make_uint4(x[4 % DP], x[5 % DP], x[6 % DP], x[7 % DP]);
-        uint32_t mn[DP];
+    }
+    #pragma unroll
+    for (int q = 0; q < DP; q++) {
+        uint32_t v = x[q];
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+        if (lane == 0) {
+            wm[w][q] = v;
+            if (tile < T) tmin[tile * DP + q] = v;
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
         #pragma unroll
         for (int q = 0; q < DP; q++) {
-            uint32_t v = x[q];
+            uint32_t v = wm[lane][q];
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
-            mn[q] = v;
-        }
-        if (lane == 0) {
-            uint4 *td = reinterpret_cast<uint4 *>(tmin + tile * DP);
-            td[0] = make_uint4(mn[0], mn[1], mn[2], mn[3]);
-            if (DP == 8) td[1] = make_uint4(mn[4 % DP], mn[5 % DP], mn[6 % DP], mn[7 % DP]);
+            if (lane == 0) smin[(long long)blockIdx.x * DP + q] = v;
         }
     }
 }
@@ -321,14 +333,13 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 template <int D>
 __host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 ? 384 : 256); }
 
-constexpr int kTileKeys = 8;                 // tile keys per lane in one selection round (<= 256 tiles)
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
 // Grid resistance of target i of query q (one warp): the first step at which
 // some candidate's projection dominates the target's projection, else K.
 template <int D, int SLOTS, bool RES>
 __device__ __forceinline__ void dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
-                                           long long T, unsigned i, uint32_t *wsteps,
+                                           const uint32_t *smin, long long T, unsigned i, uint32_t *wsteps,
                                            unsigned long long &n_tests, unsigned long long &n_checks) {
     constexpr int WS = 32 * SLOTS;
     const int lane = threadIdx.x & 31;
@@ -351,16 +362,41 @@ __device__ __forceinline__ void dom_target(const DomQuery &qy, const uint32_t *c
         // keys hold excesses >> qshift; only excesses below the window's widest width matter
         const uint32_t wmax = wsteps[wcount - 1];
         const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
-        for (long long tc = 0; tc < T && best > 0; tc += 32 * kTileKeys) {
-            // tile level: e_tile = max_i (tmin_i - t_i)^+ bounds every row's excess from
-            // below; a tile matters only while e_tile < delta[best - 1]. Tiles are visited in
-            // ascending order of e_tile (quantized to 24 bits for the key; exact test below).
-            uint32_t key[kTileKeys], ex[kTileKeys];
-            #pragma unroll
-            for (int e = 0; e < kTileKeys; e++) {
-                key[e] = kNoTile;
-                ex[e] = 0xFFFFFFFFu;
-                const long long tile = tc + 32 * e + lane;
+        // Best-first over three levels -- 1024-row super-tiles, 32-row tiles, rows --
+        // each visited in ascending order of its lower bound on the excess
+        // max_i (s_i - t_i)^+ (keys hold it >> qshift, 27 bits; exact tests below).
+        // Anything whose bound reaches delta[best - 1] is skipped.
+        const long long T2 = (T + 31) / 32;
+        for (long long sc = 0; sc < T2 && best > 0; sc += 32) {
+            uint32_t skey = kNoTile, sex = 0xFFFFFFFFu;
+            if (sc + lane < T2) {
+                uint32_t mn[D];
+                if (RES) ld_row<D>(smin, sc + lane, mn); else ldg_row<D>(smin, sc + lane, mn);
+                uint32_t emax = 0;
+                bool can = false;
+                #pragma unroll
+                for (int q = 0; q < D; q++) {
+                    emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
+                    can |= mn[q] < t[q];
+                }
+                if (can && emax < wsteps[best - 1]) {
+                    sex = emax;
+                    skey = (min(emax >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane;
+                }
+            }
+            n_checks += 32;
+            for (;;) {
+                const uint32_t mk = __reduce_min_sync(kFull, skey);
+                if (mk == kNoTile) break;
+                const uint32_t wl = wsteps[best - 1];
+                if ((mk >> 5) > min(wl >> qshift, 0x7FFFFFFu)) break;   // every super-tile left is too far
+                const int sl = (int)(mk & 31u);
+                if (lane == sl) skey = kNoTile;
+                if (__shfl_sync(kFull, sex, sl) >= wl) continue;
+                const long long sup = sc + sl;
+                // tile level inside the super-tile: lane = tile
+                uint32_t tkey = kNoTile, tex = 0xFFFFFFFFu;
+                const long long tile = sup * 32 + lane;
                 if (tile < T) {
                     uint32_t mn[D];
                     if (RES) ld_row<D>(tmin, tile, mn); else ldg_row<D>(tmin, tile, mn);
@@ -371,95 +407,88 @@ __device__ __forceinline__ void dom_target(const DomQuery &qy, const uint32_t *c
                         emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
                         can |= mn[q] < t[q];
                     }
-                    if (can && emax < wsteps[best - 1]) {
-                        ex[e] = emax;
-                        key[e] = (min(emax >> qshift, 0xFFFFFFu) << 8) | (uint32_t)(32 * e + lane);
+                    if (can && emax < wl) {
+                        tex = emax;
+                        tkey = (min(emax >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane;
                     }
-                }
-            }
-            n_checks += 32 * kTileKeys;
-            for (;;) {
-                uint32_t lm = key[0];
-                #pragma unroll
-                for (int e = 1; e < kTileKeys; e++) lm = min(lm, key[e]);
-                const uint32_t mkey = __reduce_min_sync(kFull, lm);
-                if (mkey == kNoTile) break;
-                const uint32_t wlim = wsteps[best - 1];
-                if ((mkey >> 8) > min(wlim >> qshift, 0xFFFFFFu)) break;   // every tile left is too far
-                uint32_t mine = 0xFFFFFFFFu;
-                #pragma unroll
-                for (int e = 0; e < kTileKeys; e++) {
-                    if (key[e] == mkey) { mine = ex[e]; key[e] = kNoTile; }
-                }
-                const uint32_t off = mkey & 0xFFu;
-                const uint32_t etile = __shfl_sync(kFull, mine, off & 31u);
-                if (etile >= wlim) continue;
-                const long long r0 = (tc + off) * kTileRows;
-                // candidate level: lane r looks at row r of the tile
-                uint32_t s[D];
-                if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
-                uint32_t e_r = 0;
-                bool can_r = false;
-                #pragma unroll
-                for (int q = 0; q < D; q++) {
-                    e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
-                    can_r |= s[q] < t[q];
                 }
                 n_checks += 32;
-                // a row can dominate t only at widths wider than e_r; it matters only if such
-                // a width comes before best. Rows are taken in ascending order of e_r.
-                uint32_t ckey = (can_r && e_r < wlim) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
-                                                      : 0xFFFFFFFFu;
                 for (;;) {
-                    const uint32_t ck = __reduce_min_sync(kFull, ckey);
-                    if (ck == 0xFFFFFFFFu) break;
-                    const int c = (int)(ck & 31u);
-                    if (lane == c) ckey = 0xFFFFFFFFu;
-                    const uint32_t ec = __shfl_sync(kFull, e_r, c);
-                    if (ec >= wsteps[best - 1]) {
-                        if ((ck >> 5) > min(wsteps[best - 1] >> qshift, 0x7FFFFFFu)) break;
-                        continue;
+                    const uint32_t tk = __reduce_min_sync(kFull, tkey);
+                    if (tk == kNoTile) break;
+                    const uint32_t wlim = wsteps[best - 1];
+                    if ((tk >> 5) > min(wlim >> qshift, 0x7FFFFFFu)) break;   // every tile left is too far
+                    const int tl = (int)(tk & 31u);
+                    if (lane == tl) tkey = kNoTile;
+                    if (__shfl_sync(kFull, tex, tl) >= wlim) continue;
+                    const long long r0 = (sup * 32 + tl) * kTileRows;
+                    // candidate level: lane r looks at row r of the tile
+                    uint32_t s[D];
+                    if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
+                    uint32_t e_r = 0;
+                    bool can_r = false;
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) {
+                        e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
+                        can_r |= s[q] < t[q];
                     }
-                    uint32_t sc[D];
-                    #pragma unroll
-                    for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
-                    // first slot holding a width wider than ec
-                    int jlo = 0;
-                    #pragma unroll
-                    for (int j = 0; j < SLOTS - 1; j++) jlo += (32 * j + 31 < wcount && wsteps[32 * j + 31] <= ec) ? 1 : 0;
-                    const int jhi = (best - 1) >> 5;
-                    #pragma unroll
-                    for (int j = 0; j < SLOTS; j++) {
-                        if (j < jlo || j > jhi) continue;
-                        if (!(ready & (1u << j))) {
-                            ready |= 1u << j;
-                            const int k = w0 + 32 * j + lane;
-                            const bool live = k < K;
-                            const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
-                                                  : make_uint4(1u, 0u, 0u, 1u);
-                            const uint32_t delta = mg.w;
+                    n_checks += 32;
+                    // a row can dominate t only at widths wider than e_r; it matters only if such
+                    // a width comes before best. Rows are taken in ascending order of e_r.
+                    uint32_t ckey = (can_r && e_r < wlim) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
+                                                          : 0xFFFFFFFFu;
+                    for (;;) {
+                        const uint32_t ck = __reduce_min_sync(kFull, ckey);
+                        if (ck == 0xFFFFFFFFu) break;
+                        const int c = (int)(ck & 31u);
+                        if (lane == c) ckey = 0xFFFFFFFFu;
+                        const uint32_t ec = __shfl_sync(kFull, e_r, c);
+                        if (ec >= wsteps[best - 1]) {
+                            if ((ck >> 5) > min(wsteps[best - 1] >> qshift, 0x7FFFFFFu)) break;
+                            continue;
+                        }
+                        uint32_t sc[D];
+                        #pragma unroll
+                        for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
+                        // first slot holding a width wider than ec
+                        int jlo = 0;
+                        #pragma unroll
+                        for (int j = 0; j < SLOTS - 1; j++) jlo += (32 * j + 31 < wcount && wsteps[32 * j + 31] <= ec) ? 1 : 0;
+                        const int jhi = (best - 1) >> 5;
+                        #pragma unroll
+                        for (int j = 0; j < SLOTS; j++) {
+                            if (j < jlo || j > jhi) continue;
+                            if (!(ready & (1u << j))) {
+                                ready |= 1u << j;
+                                const int k = w0 + 32 * j + lane;
+                                const bool live = k < K;
+                                const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
+                                                      : make_uint4(1u, 0u, 0u, 1u);
+                                const uint32_t delta = mg.w;
+                                #pragma unroll
+                                for (int q = 0; q < D; q++) {
+                                    const uint32_t v = qy.dir ? ~t[q] : t[q];
+                                    const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
+                                    const uint32_t uv =
+                                        lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+                                    U[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
+                                    L[j][q] = live ? (qy.dir ? ~uv : lv) : 0u;
+                                }
+                            }
+                            bool le = true, lt = false;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                const uint32_t v = qy.dir ? ~t[q] : t[q];
-                                const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
-                                const uint32_t uv =
-                                    lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
-                                U[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
-                                L[j][q] = live ? (qy.dir ? ~uv : lv) : 0u;
+                                le &= sc[q] <= U[j][q];
+                                lt |= sc[q] < L[j][q];
+                            }
+                            n_tests += 32;
+                            const unsigned msk = __ballot_sync(kFull, le & lt);
+                            if (msk) {
+                                best = min(best, 32 * j + __ffs(msk) - 1);
+                                break;
                             }
                         }
-                        bool le = true, lt = false;
-                        #pragma unroll
-                        for (int q = 0; q < D; q++) {
-                            le &= sc[q] <= U[j][q];
-                            lt |= sc[q] < L[j][q];
-                        }
-                        n_tests += 32;
-                        const unsigned msk = __ballot_sync(kFull, le & lt);
-                        if (msk) {
-                            best = min(best, 32 * j + __ffs(msk) - 1);
-                            break;
-                        }
+                        if (best == 0) break;
                     }
                     if (best == 0) break;
                 }
@@ -485,14 +514,17 @@ k_dominance(DomArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *wsteps = sm + warp * WS;
     uint32_t *stage = sm + nwarps * WS;
+    const long long T2 = (T + 31) / 32;
     const long long cand_words = T * kTileRows * DP;
-    const long long need = cand_words + T * DP;
+    const long long need = cand_words + T * DP + T2 * DP;
     const bool resident = need <= (long long)a.smem_words - (long long)nwarps * WS;
     if (resident) {
-        const long long n16a = cand_words / 4, n16b = (T * DP) / 4;
+        const long long n16a = cand_words / 4, n16b = (T * DP) / 4, n16c = (T2 * DP) / 4;
         for (long long v = threadIdx.x; v < n16a; v += blockDim.x) cp_async16(stage + 4 * v, a.q.cand + 4 * v);
         for (long long v = threadIdx.x; v < n16b; v += blockDim.x)
             cp_async16(stage + cand_words + 4 * v, a.q.tmin + 4 * v);
+        for (long long v = threadIdx.x; v < n16c; v += blockDim.x)
+            cp_async16(stage + cand_words + T * DP + 4 * v, a.q.smin + 4 * v);
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
     }
@@ -503,7 +535,8 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            dom_target<D, SLOTS, true>(a.q, stage, stage + cand_words, T, i, wsteps, n_tests, n_checks);
+            dom_target<D, SLOTS, true>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T, i, wsteps,
+                                       n_tests, n_checks);
         }
     } else {
         for (;;) {
@@ -511,7 +544,7 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            dom_target<D, SLOTS, false>(a.q, a.q.cand, a.q.tmin, T, i, wsteps, n_tests, n_checks);
+            dom_target<D, SLOTS, false>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests, n_checks);
         }
     }
     if (a.tests && lane == 0 && (n_tests | n_checks)) {
@@ -559,7 +592,8 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
         const DomQuery &q = b.q[lo];
         const long long S = *q.n_sky;
         const long long T = (S + kTileRows - 1) / kTileRows;
-        dom_target<D, SLOTS, false>(q, q.cand, q.tmin, T, (unsigned)(g - first[lo]), wsteps, n_tests, n_checks);
+        dom_target<D, SLOTS, false>(q, q.cand, q.tmin, q.smin, T, (unsigned)(g - first[lo]), wsteps, n_tests,
+                                    n_checks);
     }
 }
 
@@ -668,9 +702,10 @@ cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cuda
             if (e != cudaSuccess) return e;
         }
     }
-    const int pb = (int)std::min<int64_t>((n + 255) / 256 + 1, (int64_t)g_sm_count * 8);
-    k_permute<D><<<pb, 256, 0, st>>>(ws.sky_rows, ws.vals[0], ws.vals[1], ws.hdr,
-                                     scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.perm); note_launch();
+    const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
+    k_permute<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.sky_rows, ws.vals[0], ws.vals[1], ws.hdr,
+                                                  scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.smin,
+                                                  ws.perm); note_launch();
     return cudaGetLastError();
 }
 
@@ -792,6 +827,7 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
     DomQuery q;
     q.cand = ws.cand;
     q.tmin = ws.tmin;
+    q.smin = ws.smin;
     q.perm = ws.perm;
     q.n_sky = &ws.hdr->n_sky;
     q.magic = ws.magic;

@@ -174,6 +174,7 @@ gres_status launch_batch(gres_server *sv, Slot &sl, const std::vector<DatasetEnt
                 gres::DomQuery q;
                 q.cand = ds->cand;
                 q.tmin = ds->tmin;
+                q.smin = ds->smin;
                 q.perm = ds->perm;
                 q.n_sky = ds->n_sky;
                 q.magic = d_magic + 4 * soff[i];
