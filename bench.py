@@ -207,6 +207,34 @@ def run_reference(args):
     return 0
 
 
+# ---- whole-job numbers over ranks ----------------------------------------------------
+def _rank_reduce(x: float, op: str, device) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_max(x: float, device) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    return _rank_reduce(x, "max", device)
+
+
+def rank_sum(x: float, device) -> float:
+    """The sum of x over all ranks (x itself without a process group)."""
+    return _rank_reduce(x, "sum", device)
+
+
+def whole_job(total_ms: float, units: float, device):
+    """(slowest rank's time, units of all ranks, units of all ranks / slowest time in s)."""
+    t = rank_max(total_ms, device)
+    u = rank_sum(units, device)
+    return t, u, (u / (t / 1e3) if t > 0 else 0.0)
+
+
 # ---- our arm ------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -298,15 +326,7 @@ def run_ours(args):
     # result check: the timed steps produce the same result as the warm-up
     assert int(out[2].item()) == S and np.array_equal(out[1][:S].cpu().numpy(), step_idx)
 
-    total_eff = float(eff) * args.steps
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([total_eff], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        total_eff = float(u.item())
-    value = total_eff / (total_ms / 1e3)
+    total_ms, total_eff, value = whole_job(total_ms, float(eff) * args.steps, dev)
     ms_per_step = total_ms / args.steps
 
     # roofline of the dominant kernel (the grid-dominance kernel)
@@ -343,11 +363,7 @@ def run_ours(args):
         sk, rr = G.gres_compute_host(pinned, steps, G.MIN, cfg, ws=ws_h, out=(hs, hr), stream=stream)
     e2e_s = (time.perf_counter() - t0) / args.steps
     assert np.array_equal(rr.numpy(), step_idx)
-    e2e_s_all = e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s_all = float(t.item())
+    e2e_s_all = rank_max(e2e_s, dev)
     e2e = {"value": total_eff / args.steps / e2e_s_all, "unit": UNIT,
            "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(S * 12 + 8),
            "ms_per_step": e2e_s_all * 1e3}
@@ -401,22 +417,13 @@ def batch_problems(count=512, seed=0):
     return out, steps_log(128, 16)
 
 
-def run_batch(args):
+def _time_batch(probs, args, dev, stream):
+    """One gres_batch over probs captured in a CUDA graph; mean replay ms, launches per call,
+    clocks and the outputs."""
     import torch
     from paper_2412_02274_gb300 import gres as G
-    dev = torch.device("cuda", torch.cuda.current_device())
-    insts, steps = batch_problems()
-    K = len(steps)
-    tsteps = torch.from_numpy(steps.view(np.int32)).to(dev)
-    probs = [{"data": G.to_device_u32(data, dev), "steps": tsteps, "cfg": G.plan(G.PART_GRID)}
-             for _, _, _, data in insts]
-    stream = torch.cuda.current_stream(dev)
     outs, cinsts, ws = G.batch(probs, stream=stream)
     torch.cuda.synchronize(dev)
-    eff = 0
-    for sky, res, cnt in outs:
-        S = int(cnt.item())
-        eff += effective_tests(res[:S].cpu().numpy(), K)
     lib = G.load()
     graph = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream(dev)
@@ -441,7 +448,40 @@ def run_batch(args):
         torch.cuda.synchronize(dev)
         t_ms.append(a.elapsed_time(b))
     clocks = sampler.stop()
-    ms = float(np.mean(t_ms))
+    del graph
+    return float(np.mean(t_ms)), per_call, clocks, outs
+
+
+def run_batch(args):
+    import torch
+    from paper_2412_02274_gb300 import gres as G
+    from paper_2412_02274_gb300.autotune import Autotuner
+    dev = torch.device("cuda", torch.cuda.current_device())
+    insts, steps = batch_problems()
+    K = len(steps)
+    tsteps = torch.from_numpy(steps.view(np.int32)).to(dev)
+    datas = [G.to_device_u32(data, dev) for _, _, _, data in insts]
+    stream = torch.cuda.current_stream(dev)
+    # default plan (Grid, about 256 cells, 8 slots) for every instance
+    dflt = [{"data": x, "steps": tsteps, "cfg": G.plan(G.PART_GRID)} for x in datas]
+    ms_default, _, _, outs_d = _time_batch(dflt, args, dev, stream)
+    # autotuned plans: candidates timed per size class (d, power-of-two bucket of n) on
+    # the two largest instances of the class, outside the timed region, scored as part
+    # of a batch (the dominance stage plus the overlapped other stages / 16)
+    t0 = time.time()
+    tuner = Autotuner(objective="batch")
+    table = tuner.tune(datas, steps, samples_per_class=2)
+    tune_s = time.time() - t0
+    probs = [{"data": x, "steps": tsteps, "cfg": tuner.plan_for(int(x.shape[0]), int(x.shape[1]))}
+             for x in datas]
+    ms, per_call, clocks, outs = _time_batch(probs, args, dev, stream)
+    eff = 0
+    for (sky, res, cnt), (sky_d, res_d, cnt_d) in zip(outs, outs_d):
+        S = int(cnt.item())
+        r = res[:S].cpu().numpy()
+        if S != int(cnt_d.item()) or not np.array_equal(r, res_d[:S].cpu().numpy()):
+            raise RuntimeError("tuned and default plans disagree")
+        eff += effective_tests(r, K)
     # the same 512 problems one at a time (one gres_compute per instance, direct calls)
     wss = {}
     for _ in range(max(1, args.warmup // 2)):
@@ -461,18 +501,26 @@ def run_batch(args):
     b.record(stream)
     torch.cuda.synchronize(dev)
     ms_single = a.elapsed_time(b)
+    picks = {}
+    for name in table.values():
+        picks[name] = picks.get(name, 0) + 1
     line = {"metric": "gres instances/s (512 uneven instances per step)", "value": len(probs) / (ms / 1e3),
             "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": "batch-512", "instances": len(probs), "widths": K,
                        "n_range": [1000, 200000], "d_range": [2, 8], "distributions": ["uni", "ant", "clu"],
-                       "launch": "one gres_batch captured in a CUDA graph",
+                       "launch": "one gres_batch captured in a CUDA graph", "plans": "autotuned",
                        "l2": "256 MiB write between timed steps"},
             "effective_tests_per_s": eff / (ms / 1e3),
+            "default_plan": {"ms": ms_default, "instances_per_s": len(probs) / (ms_default / 1e3)},
+            "autotune": {"classes": len(table), "seconds": tune_s, "picks": picks},
             "one_at_a_time": {"ms": ms_single, "instances_per_s": len(probs) / (ms_single / 1e3),
                               "speedup_of_batch": ms_single / ms},
             "gpu_launches": per_call * args.steps, "clocks": clocks}
+    if args.tune_table:
+        with open(args.tune_table, "w") as f:
+            f.write(tuner.to_json())
     print(json.dumps(line), flush=True)
     return 0
 
@@ -577,6 +625,7 @@ def main(argv=None):
                          "(--no-graph: direct calls)")
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--tune-table", default="", help="batch-512: write the autotuned plan table (JSON) here")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -223,9 +223,13 @@ gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, si
  * slot frees up it takes up to max_batch queued queries (arrival order) and
  * runs them as one batch: one copy of their widths, one kernel for their
  * division constants, one grid-dominance launch per dimensionality over all
- * their targets, one copy of the results. Queries that arrive while batches
- * run are admitted as slots free up. Results are identical to gres_query /
- * gres_compute (the kernels are deterministic per target). */
+ * their targets, one copy of the results. A query on a skyline larger than
+ * chunk_targets is answered in pieces of at most chunk_targets targets, one
+ * piece per batch, after which the query goes to the back of the queue:
+ * batches stay short and queries on small skylines do not wait behind a
+ * large one. Queries that arrive while batches run are admitted as slots
+ * free up. Results are identical to gres_query / gres_compute (the kernels
+ * are deterministic per target). */
 typedef struct gres_server gres_server;
 typedef struct {
     int32_t max_batch;       /* queries per batch, 1..256 (0: 64)                   */
@@ -234,6 +238,8 @@ typedef struct {
     int32_t max_k;           /* longest step list accepted (0: 4096)                */
     int32_t start_paused;    /* nonzero: queue queries but start no batch until
                                 gres_serve_resume (admission control, tests)        */
+    int32_t chunk_targets;   /* targets per piece of a query (0: 65536; < 0: whole
+                                queries, no pieces)                                 */
 } gres_serve_cfg;
 
 /* Creates a server on the current device. hbm_budget_bytes bounds the device
@@ -269,6 +275,35 @@ gres_status gres_serve_stats(gres_server *sv, uint64_t *batches, uint64_t *queri
 /* Stops the scheduler (queued queries are dropped, running batches finish)
  * and frees everything the server holds. */
 gres_status gres_serve_destroy(gres_server *sv);
+
+/* Partitioning of a candidate set (Sec. 3.1) into the tile layout that the
+ * grid-dominance kernel reads: the same kernels gres_compute runs on the
+ * skyline, here on the caller's rows as they are (no skyline step).
+ *   d_rows      device, n*d uint32, row-major (not modified).
+ *   cfg         scheme GRID / ANGULAR / SLICED / NONE with m, p, slice_dim
+ *               (NULL: GRID with about 256 cells); reps, slots, flags unused.
+ *   d_part      device, n int64: partition number of each row on canonical
+ *               coordinates x = c - min c (c = v for GRES_MIN, 2^32-1-v for
+ *               GRES_MAX; min and max over the n rows, per attribute):
+ *                 GRID     sum_i floor(x_i m / (max_i - min_i + 1)) m^i;
+ *                 ANGULAR  sum_{i<d-1} b_i m^i with b_i the number of angles
+ *                          j pi / 2m (j = 1 .. m-1) that
+ *                          phi_i = atan2(sqrt(x_{i+1}^2 + ... + x_{d-1}^2), x_i)
+ *                          reaches (Eq. 1), decided exactly as
+ *                          Y 2^32 >= X round(tan^2(j pi / 2m) 2^32);
+ *                 SLICED   floor(r p / n), r the rank of the row in the order
+ *                          of x_{slice_dim} (ties: lower row first);
+ *                 NONE     0.
+ *   d_order     device, n uint32: the rows in tile order (position -> row);
+ *               partition numbers never decrease along it.
+ *   d_tile_min  device, ceil(n/32)*d uint32: per 32-row tile of that order,
+ *               the per-attribute minimum of the canonical values c.
+ * Workspace: gres_workspace_size(n, d, 1). The order inside a partition
+ * (a spatial order) is unspecified. GRES_EINVAL on bad arguments before
+ * anything is queued. */
+gres_status gres_partition(const uint32_t *d_rows, int64_t n, int32_t d, int32_t dir,
+                           const gres_plan_cfg *cfg, void *d_ws, size_t ws_bytes,
+                           int64_t *d_part, uint32_t *d_order, uint32_t *d_tile_min, void *stream);
 
 /* Grid projection (Sec. 2) of `count` values at each of k widths:
  * d_out[j*count + i] = floor(d_values[i] / h_steps[j]) (the paper's

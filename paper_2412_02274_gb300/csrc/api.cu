@@ -356,6 +356,33 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
     return GRES_OK;
 }
 
+gres_status gres_partition(const uint32_t *d_rows, int64_t n, int32_t d, int32_t dir,
+                           const gres_plan_cfg *cfg, void *d_ws, size_t ws_bytes,
+                           int64_t *d_part, uint32_t *d_order, uint32_t *d_tile_min, void *stream) {
+    gres_status s = check_dims(n, d);
+    if (s != GRES_OK) return s;
+    if (dir != GRES_MIN && dir != GRES_MAX) return fail(GRES_EINVAL, "dir must be GRES_MIN or GRES_MAX");
+    gres_plan_cfg plan;
+    s = check_plan(cfg, d, &plan);
+    if (s != GRES_OK) return s;
+    if (n > 0 && (!d_rows || !d_part || !d_order || !d_tile_min))
+        return fail(GRES_EINVAL, "d_rows / d_part / d_order / d_tile_min is NULL");
+    const size_t need = gres::workspace_layout(n, d, 1, nullptr, nullptr);
+    if (!ws_ok(d_ws, ws_bytes, need)) return fail(GRES_EINVAL, "workspace too small, NULL or not 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gres::Workspace ws;
+    gres::workspace_layout(n, d, 1, d_ws, &ws);
+    cudaError_t e = gres::launch_init(ws, n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    e = gres::launch_load_candidates(d_rows, n, d, dir, ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "load");
+    e = gres::launch_partition(d, plan, n, ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "partition");
+    e = gres::launch_partition_out(d, plan.scheme, n, ws, d_part, d_order, d_tile_min, st);
+    if (e != cudaSuccess) return cuda_fail(e, "partition output");
+    return GRES_OK;
+}
+
 gres_status gres_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps,
                        int32_t k, uint32_t *d_out, void *stream) {
     if (count < 0) return fail(GRES_EINVAL, "count must be >= 0");

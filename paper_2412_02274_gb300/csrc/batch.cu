@@ -151,7 +151,7 @@ gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int3
     const size_t b_tmin = align256(4 * (size_t)DP * (size_t)(T > 0 ? T : 1));
     const int64_t T2 = (T + 31) / 32;
     const size_t b_smin = align256(4 * (size_t)DP * (size_t)(T2 > 0 ? T2 : 1));
-    const size_t bytes = b_sky + b_perm + b_cand + b_tmin + b_smin + 256;
+    const size_t bytes = b_sky + 2 * b_perm + b_cand + b_tmin + b_smin + 256;
     void *mem = nullptr;
     e = cudaMalloc(&mem, bytes);
     if (e != cudaSuccess) {
@@ -172,6 +172,8 @@ gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int3
     char *m = static_cast<char *>(mem);
     ds->sky_idx = reinterpret_cast<int64_t *>(m);
     ds->perm = reinterpret_cast<uint32_t *>(m + b_sky);
+    ds->iperm = reinterpret_cast<uint32_t *>(m + b_sky + b_perm);
+    m += b_perm;
     ds->cand = reinterpret_cast<uint32_t *>(m + b_sky + b_perm);
     ds->tmin = reinterpret_cast<uint32_t *>(m + b_sky + b_perm + b_cand);
     ds->smin = reinterpret_cast<uint32_t *>(m + b_sky + b_perm + b_cand + b_tmin);
@@ -180,6 +182,7 @@ gres_status gres_dataset_create(const uint32_t *data, int64_t n, int32_t d, int3
     if (e == cudaSuccess && S > 0) {
         e = cudaMemcpyAsync(ds->sky_idx, tmp_sky, 8 * (size_t)S, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ds->perm, ws.perm, 4 * (size_t)S, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = gres::launch_invert_perm(ds->perm, S, ds->iperm, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ds->cand, ws.cand, 4 * (size_t)DP * T * gres::kTileRows, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess)

@@ -201,6 +201,11 @@ struct DomQuery {
     int32_t *out;             // result per skyline position
     int K;
     int dir;
+    // Target range (resident datasets): when iperm is set, the targets are the
+    // skyline positions t0 .. t0 + tn - 1 (iperm: skyline -> partition
+    // position) and the result of position j goes to out[j - t0].
+    const uint32_t *iperm = nullptr;
+    unsigned t0 = 0, tn = 0;
 };
 
 // Division constants to make on the device for one query (k_make_magic).
@@ -214,6 +219,9 @@ struct MagicJob {
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
 // Uploads the widths and their division constants and resets the header.
 cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st);
+// Sorts of at most kClusterSortMax items run as one launch of one thread-block
+// cluster; larger ones as three kernels per digit pass.
+constexpr int64_t kClusterSortMax = 131072;
 cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
                               int max_passes, cudaStream_t st);
 cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,
@@ -224,12 +232,22 @@ cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir,
                               unsigned long long *d_tests, cudaStream_t st);
 // The candidate partitioning of the skyline in ws (cand, tmin, perm).
 cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st);
+// The caller's rows as the candidate set (canonical padded rows into
+// sky_rows, their range into lo/hi, S = n), for gres_partition.
+cudaError_t launch_load_candidates(const uint32_t *d_rows, int64_t n, int d, int dir, Workspace &ws,
+                                   cudaStream_t st);
+// Partition numbers by row, the tile order and the tile minima (d words per
+// tile) after launch_partition.
+cudaError_t launch_partition_out(int d, int scheme, int64_t n, Workspace &ws, int64_t *d_part,
+                                 uint32_t *d_order, uint32_t *d_tile_min, cudaStream_t st);
 // The grid-dominance kernel for one query; *counter must be 0.
 cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,
                              unsigned long long *tests, cudaStream_t st);
 // One launch for up to 256 queries of the same d; *counter must be 0.
 cudaError_t launch_dominance_batch(int d, int slots, const DomQuery *qs, int count, unsigned *counter,
                                    cudaStream_t st);
+// iperm[perm[i]] = i for i < S (the inverse of a dataset's tile order).
+cudaError_t launch_invert_perm(const uint32_t *perm, int64_t S, uint32_t *iperm, cudaStream_t st);
 // Device-side division constants (and counter resets) for many queries.
 cudaError_t launch_make_magic(const MagicJob *jobs, int count, cudaStream_t st);
 // Widths from the host into d_steps / d_magic; zeroes *zero when given.
@@ -253,6 +271,7 @@ struct gres_dataset {
     size_t bytes;
     int64_t *sky_idx;     // S: skyline rows, ascending
     uint32_t *perm;       // S: partition position -> skyline position
+    uint32_t *iperm;      // S: skyline position -> partition position
     uint32_t *cand;       // T*32 rows of DP words (partition order, sentinel-padded)
     uint32_t *tmin;       // T rows of DP words
     uint32_t *smin;       // ceil(T / 32) rows of DP words

@@ -317,6 +317,63 @@ k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1
     }
 }
 
+// gres_partition: the caller's rows, canonical and padded, as the candidate
+// set; their per-attribute range into lo/hi and S = n.
+template <int D>
+__global__ void k_load_candidates(const uint32_t *rows, int dir, long long n, uint32_t *sky_rows,
+                                  WsHeader *h) {
+    constexpr int DP = padded_dims(D);
+    if (blockIdx.x == 0 && threadIdx.x == 0) h->n_sky = n;
+    uint32_t lo[D], hi[D];
+    #pragma unroll
+    for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        uint32_t y[DP];
+        #pragma unroll
+        for (int q = 0; q < DP; q++) y[q] = q < D ? canon(rows[j * D + (q < D ? q : 0)], dir) : 0u;
+        #pragma unroll
+        for (int q = 0; q < D; q++) { lo[q] = min(lo[q], y[q]); hi[q] = max(hi[q], y[q]); }
+        uint4 *dst = reinterpret_cast<uint4 *>(sky_rows + j * DP);
+        dst[0] = make_uint4(y[0], y[1], y[2], y[3]);
+        if (DP == 8) dst[1] = make_uint4(y[4 % DP], y[5 % DP], y[6 % DP], y[7 % DP]);
+    }
+    #pragma unroll
+    for (int q = 0; q < D; q++) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[q] = min(lo[q], __shfl_xor_sync(kFull, lo[q], o));
+            hi[q] = max(hi[q], __shfl_xor_sync(kFull, hi[q], o));
+        }
+        if ((threadIdx.x & 31) == 0 && lo[q] <= hi[q]) {
+            atomicMin(&h->lo[q], lo[q]);
+            atomicMax(&h->hi[q], hi[q]);
+        }
+    }
+}
+
+// gres_partition outputs: partition number by row (the sort key's high bits),
+// the tile order, and the tile minima with d words per tile.
+template <int D>
+__global__ void k_partition_out(const WsHeader *h, const unsigned long long *keys0,
+                                const unsigned long long *keys1, const uint32_t *perm,
+                                const uint32_t *tmin, int scheme, long long n, int64_t *part,
+                                uint32_t *order, uint32_t *tile_min) {
+    constexpr int DP = padded_dims(D);
+    const unsigned long long *keys = h->sorted_sel ? keys1 : keys0;
+    const long long T = (n + kTileRows - 1) / kTileRows;
+    const long long total = n > T * D ? n : T * D;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += stride) {
+        if (r < n) {
+            const uint32_t j = perm[r];
+            order[r] = j;
+            part[j] = scheme == GRES_PART_NONE ? 0 : (int64_t)(keys[r] >> 16);
+        }
+        if (r < T * D) tile_min[r] = tmin[(r / D) * DP + r % D];
+    }
+}
+
 // ---- the pairwise grid-dominance kernel ------------------------------------
 struct DomArgs {
     DomQuery q;
@@ -335,10 +392,11 @@ __host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 
 
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
-// Grid resistance of target i of query q (one warp): the first step at which
-// some candidate's projection dominates the target's projection, else K.
+// Grid resistance of the target at partition position i of query q (one
+// warp; every lane returns it): the first step at which some candidate's
+// projection dominates the target's projection, else K.
 template <int D, int SLOTS, bool RES>
-__device__ __forceinline__ void dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
+__device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
                                            const uint32_t *smin, long long T, unsigned i, uint32_t *wsteps,
                                            unsigned long long &n_tests, unsigned long long &n_checks) {
     constexpr int WS = 32 * SLOTS;
@@ -498,7 +556,7 @@ __device__ __forceinline__ void dom_target(const DomQuery &qy, const uint32_t *c
         __syncwarp();
         if (best < wcount) { result = w0 + best; break; }
     }
-    if (lane == 0) qy.out[qy.perm[i]] = result;
+    return result;
 }
 
 template <int D, int SLOTS>
@@ -535,8 +593,9 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            dom_target<D, SLOTS, true>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T, i, wsteps,
-                                       n_tests, n_checks);
+            const int r = dom_target<D, SLOTS, true>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T,
+                                                     i, wsteps, n_tests, n_checks);
+            if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
     } else {
         for (;;) {
@@ -544,7 +603,9 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            dom_target<D, SLOTS, false>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests, n_checks);
+            const int r = dom_target<D, SLOTS, false>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests,
+                                                      n_checks);
+            if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
     }
     if (a.tests && lane == 0 && (n_tests | n_checks)) {
@@ -555,7 +616,8 @@ k_dominance(DomArgs a) {
 
 // Many queries (same D) in one launch: work items are the (query, target)
 // pairs of all queries, handed out by one counter; candidates are read through
-// L1 (each query has its own candidate set).
+// L1 (each query has its own candidate set). A query with iperm set takes
+// only its target range (see DomQuery).
 constexpr int kMaxBatch = 256;
 struct DomBatch {
     int count;
@@ -573,7 +635,10 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
     uint32_t *wsteps = sm + warp * WS;
     if (threadIdx.x == 0) {
         unsigned long long run = 0;
-        for (int j = 0; j < b.count; j++) { first[j] = run; run += (unsigned long long)*b.q[j].n_sky; }
+        for (int j = 0; j < b.count; j++) {
+            first[j] = run;
+            run += b.q[j].iperm ? (unsigned long long)b.q[j].tn : (unsigned long long)*b.q[j].n_sky;
+        }
         first[b.count] = run;
     }
     __syncthreads();
@@ -592,9 +657,17 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
         const DomQuery &q = b.q[lo];
         const long long S = *q.n_sky;
         const long long T = (S + kTileRows - 1) / kTileRows;
-        dom_target<D, SLOTS, false>(q, q.cand, q.tmin, q.smin, T, (unsigned)(g - first[lo]), wsteps, n_tests,
-                                    n_checks);
+        const unsigned local = (unsigned)(g - first[lo]);
+        const unsigned i = q.iperm ? __ldg(q.iperm + q.t0 + local) : local;
+        const int r = dom_target<D, SLOTS, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests, n_checks);
+        if (lane == 0) q.out[q.iperm ? local : q.perm[i]] = r;
     }
+}
+
+__global__ void k_invert_perm(const uint32_t *perm, long long S, uint32_t *iperm) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += stride)
+        iperm[perm[i]] = (uint32_t)i;
 }
 
 // Division constants of K widths on the device (Granlund & Montgomery; the
@@ -783,6 +856,38 @@ cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspa
 #define GRES_PART(D) partition_d<D>(cfg, n, ws, st)
     GRES_DISPATCH_D(d, GRES_PART)
 #undef GRES_PART
+}
+
+cudaError_t launch_invert_perm(const uint32_t *perm, int64_t S, uint32_t *iperm, cudaStream_t st) {
+    if (S == 0) return cudaSuccess;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>((S + 255) / 256, (int64_t)g_sm_count * 4);
+    k_invert_perm<<<blocks, 256, 0, st>>>(perm, (long long)S, iperm); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_candidates(const uint32_t *d_rows, int64_t n, int d, int dir, Workspace &ws,
+                                   cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count * 4);
+#define GRES_LOAD(D) (k_load_candidates<D><<<blocks, 256, 0, st>>>(d_rows, dir, (long long)n, ws.sky_rows, ws.hdr), \
+                      note_launch(), cudaGetLastError())
+    GRES_DISPATCH_D(d, GRES_LOAD)
+#undef GRES_LOAD
+}
+
+cudaError_t launch_partition_out(int d, int scheme, int64_t n, Workspace &ws, int64_t *d_part,
+                                 uint32_t *d_order, uint32_t *d_tile_min, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t total = std::max<int64_t>(n, (n + kTileRows - 1) / kTileRows * d);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)g_sm_count * 4);
+#define GRES_OUT(D) (k_partition_out<D><<<blocks, 256, 0, st>>>(ws.hdr, ws.keys[0], ws.keys[1], ws.perm, \
+                     ws.tmin, scheme, (long long)n, d_part, d_order, d_tile_min), note_launch(), cudaGetLastError())
+    GRES_DISPATCH_D(d, GRES_OUT)
+#undef GRES_OUT
 }
 
 cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,

@@ -4,13 +4,17 @@
 // in device memory within an HBM budget. Queries (a dataset and a step list)
 // queue on the host. A scheduler thread keeps up to `max_inflight` batches on
 // the GPU: whenever a slot is free it takes up to `max_batch` pending queries
-// in arrival order and runs them as one batch on the slot's stream -- one
-// copy of all their widths, one kernel for their division constants, one
+// in queue order and runs them as one batch on the slot's stream -- one copy
+// of all their widths, one kernel for their division constants, one
 // grid-dominance launch per dimensionality over all their targets, and one
-// copy of all results back. Queries that arrive while batches run are
-// admitted as soon as a slot frees up, so their work overlaps with the
-// batches already on the device. Completion is detected with cudaEventQuery
-// and host condition variables: nothing waits on the device.
+// copy of all results back. A query contributes one piece to a batch: at most
+// `chunk_targets` of its targets (a range of skyline positions); if targets
+// are left it goes to the back of the queue, so a query on a very large
+// skyline is spread over many short batches instead of holding up everything
+// queued behind it. Queries that arrive while batches run are admitted as soon
+// as a slot frees up, so their work overlaps with the batches already on the
+// device. Completion is detected with cudaEventQuery and host condition
+// variables: nothing waits on the device.
 #include "gres_internal.cuh"
 
 #include <algorithm>
@@ -42,11 +46,21 @@ struct Query {
     int32_t dataset = -1;
     std::vector<uint32_t> steps;
     int64_t S = 0;
-    std::vector<int32_t> result;
+    std::vector<int32_t> result;   // S entries, filled piece by piece
+    int64_t next = 0;              // first target not yet handed to a batch
+    int outstanding = 0;           // pieces on the GPU
+    uint64_t last_batch = 0;       // the batch that took its latest piece
+    bool queued = false;           // in the pending queue
     bool done = false;
     bool cancelled = false;
     gres_status status = GRES_OK;
     Clock::time_point t_submit, t_done;
+};
+
+// Targets [t0, t0 + tn) of a query, in one batch.
+struct Piece {
+    std::shared_ptr<Query> q;
+    int64_t t0 = 0, tn = 0;
 };
 
 struct DatasetEntry {
@@ -69,7 +83,7 @@ struct Slot {
     uint32_t *h_steps = nullptr;
     int32_t *h_res = nullptr;
     size_t h_res_cap = 0;
-    std::vector<std::shared_ptr<Query>> batch;
+    std::vector<Piece> batch;
     std::vector<size_t> res_off;
 };
 
@@ -94,6 +108,7 @@ struct gres_server {
     bool paused = false;
     gres_status worker_error = GRES_OK;
     std::string worker_message;
+    uint64_t next_batch = 1;
     // statistics
     unsigned long long n_batches = 0, n_queries = 0, n_launches = 0;
 };
@@ -147,11 +162,12 @@ gres_status launch_batch(gres_server *sv, Slot &sl, const std::vector<DatasetEnt
     size_t total_k = 0, total_s = 0;
     sl.res_off.assign(sl.batch.size(), 0);
     for (size_t i = 0; i < sl.batch.size(); i++) {
+        const Query &qq = *sl.batch[i].q;
         soff[i] = total_k;
-        std::memcpy(sl.h_steps + total_k, sl.batch[i]->steps.data(), 4 * sl.batch[i]->steps.size());
-        total_k += sl.batch[i]->steps.size();
+        std::memcpy(sl.h_steps + total_k, qq.steps.data(), 4 * qq.steps.size());
+        total_k += qq.steps.size();
         sl.res_off[i] = total_s;
-        total_s += (size_t)sl.batch[i]->S;
+        total_s += (size_t)sl.batch[i].tn;
     }
     cudaError_t e = cudaMemcpyAsync(d_steps, sl.h_steps, 4 * total_k, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return cuda_fail(e, "serve steps");
@@ -159,7 +175,7 @@ gres_status launch_batch(gres_server *sv, Slot &sl, const std::vector<DatasetEnt
     if (e != cudaSuccess) return cuda_fail(e, "serve counters");
     std::vector<gres::MagicJob> jobs(sl.batch.size());
     for (size_t i = 0; i < sl.batch.size(); i++)
-        jobs[i] = {d_steps + soff[i], d_magic + 4 * soff[i], (int)sl.batch[i]->steps.size(), nullptr};
+        jobs[i] = {d_steps + soff[i], d_magic + 4 * soff[i], (int)sl.batch[i].q->steps.size(), nullptr};
     e = gres::launch_make_magic(jobs.data(), (int)jobs.size(), sl.stream);
     if (e != cudaSuccess) return cuda_fail(e, "serve constants");
     sv->n_launches += 1 + (jobs.size() + 255) / 256;
@@ -169,7 +185,7 @@ gres_status launch_batch(gres_server *sv, Slot &sl, const std::vector<DatasetEnt
             std::vector<gres::DomQuery> qs;
             for (size_t i = 0; i < sl.batch.size(); i++) {
                 const DatasetEntry &de = dsv[i];
-                if (de.d != d || de.slots != slots || de.S == 0) continue;
+                if (de.d != d || de.slots != slots || sl.batch[i].tn == 0) continue;
                 const gres_dataset *ds = de.ds;
                 gres::DomQuery q;
                 q.cand = ds->cand;
@@ -180,8 +196,11 @@ gres_status launch_batch(gres_server *sv, Slot &sl, const std::vector<DatasetEnt
                 q.magic = d_magic + 4 * soff[i];
                 q.steps = d_steps + soff[i];
                 q.out = d_res + sl.res_off[i];
-                q.K = (int)sl.batch[i]->steps.size();
+                q.K = (int)sl.batch[i].q->steps.size();
                 q.dir = de.dir;
+                q.iperm = ds->iperm;
+                q.t0 = (unsigned)sl.batch[i].t0;
+                q.tn = (unsigned)sl.batch[i].tn;
                 qs.push_back(q);
             }
             for (size_t off = 0; off < qs.size(); off += 256) {
@@ -202,22 +221,41 @@ gres_status launch_batch(gres_server *sv, Slot &sl, const std::vector<DatasetEnt
     return e == cudaSuccess ? GRES_OK : cuda_fail(e, "serve event");
 }
 
+// Marks a query finished (lock held).
+void complete(gres_server *sv, Query &q, gres_status st) {
+    q.status = q.cancelled ? GRES_EINVAL : st;
+    q.done = true;
+    q.t_done = Clock::now();
+    auto it = sv->datasets.find(q.dataset);
+    if (it != sv->datasets.end()) it->second.pending--;
+    if (q.cancelled) sv->tickets.erase(q.ticket);
+    sv->n_queries++;
+}
+
+// Removes a query from the pending queue (lock held).
+void unqueue(gres_server *sv, const std::shared_ptr<Query> &q) {
+    for (auto p = sv->pending.begin(); p != sv->pending.end(); ++p)
+        if (*p == q) { sv->pending.erase(p); break; }
+    q->queued = false;
+}
+
 void finish_batch(gres_server *sv, Slot &sl, gres_status st) {
     // lock held
-    const auto now = Clock::now();
     for (size_t i = 0; i < sl.batch.size(); i++) {
-        auto &q = sl.batch[i];
-        if (st == GRES_OK && !q->cancelled)
-            q->result.assign(sl.h_res + sl.res_off[i], sl.h_res + sl.res_off[i] + q->S);
-        q->status = q->cancelled ? GRES_EINVAL : st;
-        q->done = true;
-        q->t_done = now;
-        auto it = sv->datasets.find(q->dataset);
-        if (it != sv->datasets.end()) it->second.pending--;
-        if (q->cancelled) sv->tickets.erase(q->ticket);
+        Piece &pc = sl.batch[i];
+        Query &q = *pc.q;
+        q.outstanding--;
+        if (q.done) continue;
+        if (st != GRES_OK && q.status == GRES_OK) q.status = st;
+        if (q.status == GRES_OK && !q.cancelled && pc.tn > 0)
+            std::memcpy(q.result.data() + pc.t0, sl.h_res + sl.res_off[i], 4 * (size_t)pc.tn);
+        // a failed piece fails the query and a cancelled query takes no more
+        // pieces; either ends when its last piece in flight comes back
+        const bool ended = q.status != GRES_OK || q.cancelled;
+        if (ended && q.queued) unqueue(sv, pc.q);
+        if (q.outstanding == 0 && (ended || q.next == q.S)) complete(sv, q, q.status);
     }
     sv->n_batches++;
-    sv->n_queries += sl.batch.size();
     sl.batch.clear();
     sl.busy = false;
 }
@@ -250,14 +288,26 @@ void worker_main(gres_server *sv) {
             if (sv->pending.empty()) break;
             std::vector<DatasetEntry> dsv;
             size_t need = 0;
+            const uint64_t bid = sv->next_batch++;
             while (!sv->pending.empty() && (int)sl.batch.size() < sv->cfg.max_batch) {
                 auto q = sv->pending.front();
-                if (q->cancelled) { sv->pending.pop_front(); continue; }
+                if (q->last_batch == bid) break;   // the queue came round: one piece per query per batch
                 sv->pending.pop_front();
+                q->queued = false;
+                if (q->cancelled) continue;
                 const DatasetEntry &de = sv->datasets.at(q->dataset);
-                sl.batch.push_back(q);
+                const int64_t left = q->S - q->next;
+                const int64_t tn = sv->cfg.chunk_targets > 0 ? std::min<int64_t>(left, sv->cfg.chunk_targets) : left;
+                sl.batch.push_back(Piece{q, q->next, tn});
                 dsv.push_back(de);
-                need += (size_t)q->S;
+                q->next += tn;
+                q->outstanding++;
+                q->last_batch = bid;
+                need += (size_t)tn;
+                if (q->next < q->S) {
+                    sv->pending.push_back(q);
+                    q->queued = true;
+                }
             }
             if (sl.batch.empty()) break;
             gres_status st = slot_reserve(sv, sl, std::max<size_t>(need, 1));
@@ -299,6 +349,7 @@ gres_status gres_serve_create(size_t hbm_budget_bytes, const gres_serve_cfg *cfg
     if (c.max_inflight == 0) c.max_inflight = 2;
     if (c.queue_capacity == 0) c.queue_capacity = 1 << 16;
     if (c.max_k == 0) c.max_k = 4096;
+    if (c.chunk_targets == 0) c.chunk_targets = 65536;
     if (c.max_batch < 1 || c.max_batch > 256) return fail(GRES_EINVAL, "max_batch must be in [1, 256]");
     if (c.max_inflight < 1 || c.max_inflight > 16) return fail(GRES_EINVAL, "max_inflight must be in [1, 16]");
     if (c.queue_capacity < 1) return fail(GRES_EINVAL, "queue_capacity must be >= 1");
@@ -339,7 +390,8 @@ gres_status gres_serve_add_dataset(gres_server *sv, const uint32_t *data, int64_
     cudaStreamDestroy(st);
     if (s != GRES_OK) return s;
     std::lock_guard<std::mutex> lock(sv->mu);
-    const size_t extra = 4 * (size_t)ds->S * (size_t)sv->cfg.max_batch * sv->slots.size();
+    const int64_t piece = sv->cfg.chunk_targets > 0 ? std::min<int64_t>(ds->S, sv->cfg.chunk_targets) : ds->S;
+    const size_t extra = 4 * (size_t)piece * (size_t)sv->cfg.max_batch * sv->slots.size();
     if (sv->used + ds->bytes + extra > sv->budget) {
         gres_dataset_destroy(ds);
         return fail(GRES_ENOMEM, "serve: dataset exceeds the HBM budget");
@@ -388,11 +440,13 @@ gres_status gres_serve_submit(gres_server *sv, int32_t dataset_id, const uint32_
         if (it == sv->datasets.end()) return fail(GRES_EINVAL, "no such dataset");
         if ((int64_t)sv->pending.size() >= sv->cfg.queue_capacity) return fail(GRES_EAGAIN, "serve: queue full");
         q->S = it->second.S;
+        q->result.assign((size_t)q->S, 0);
         q->ticket = sv->next_ticket++;
         q->t_submit = Clock::now();
         it->second.pending++;
         sv->tickets[q->ticket] = q;
         sv->pending.push_back(q);
+        q->queued = true;
         *out_ticket = q->ticket;
     }
     sv->cv_work.notify_one();
@@ -406,6 +460,7 @@ gres_status gres_serve_poll(gres_server *sv, uint64_t ticket, int32_t *h_step_id
     auto it = sv->tickets.find(ticket);
     if (it == sv->tickets.end()) return fail(GRES_EINVAL, "unknown ticket");
     std::shared_ptr<Query> q = it->second;
+    if (q->cancelled) return fail(GRES_EINVAL, "query was cancelled");
     if (!q->done && timeout_us != 0) {
         auto pred = [&] { return q->done; };
         if (timeout_us < 0) sv->cv_done.wait(lock, pred);
@@ -452,18 +507,10 @@ gres_status gres_serve_cancel(gres_server *sv, uint64_t ticket) {
     std::shared_ptr<Query> q = it->second;
     if (q->done) return fail(GRES_EINVAL, "query already finished");
     q->cancelled = true;
-    // still queued: drop it now; in flight: its results are discarded on completion
-    for (auto p = sv->pending.begin(); p != sv->pending.end(); ++p) {
-        if ((*p)->ticket == ticket) {
-            sv->pending.erase(p);
-            q->done = true;
-            q->status = GRES_EINVAL;
-            auto d = sv->datasets.find(q->dataset);
-            if (d != sv->datasets.end()) d->second.pending--;
-            sv->tickets.erase(ticket);
-            break;
-        }
-    }
+    // nothing on the GPU: drop it now; pieces in flight: it ends with the last one
+    if (q->queued) unqueue(sv, q);
+    if (q->outstanding == 0) complete(sv, *q, GRES_EINVAL);
+    sv->cv_done.notify_all();
     return GRES_OK;
 }
 

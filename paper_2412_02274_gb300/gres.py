@@ -49,7 +49,7 @@ class PlanCfg(ctypes.Structure):
 class ServeCfg(ctypes.Structure):
     """``gres_serve_cfg``."""
     _fields_ = [("max_batch", _i32), ("max_inflight", _i32), ("queue_capacity", _i32), ("max_k", _i32),
-                ("start_paused", _i32)]
+                ("start_paused", _i32), ("chunk_targets", _i32)]
 
 
 class Instance(ctypes.Structure):
@@ -86,6 +86,8 @@ def load():
         lib.gres_compute_host.argtypes = [_p, _i64, _i32, _i32, _p, _i32, ctypes.POINTER(PlanCfg),
                                           _p, _size, _p, _p, _p, _p]
         lib.gres_gproj.argtypes = [_p, _i64, _p, _i32, _p, _p]
+        lib.gres_partition.argtypes = [_p, _i64, _i32, _i32, ctypes.POINTER(PlanCfg), _p, _size,
+                                       _p, _p, _p, _p]
         lib.gres_udiv_magic.argtypes = [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                                         ctypes.POINTER(_u32)]
         lib.gres_launch_count.restype = ctypes.c_ulonglong
@@ -305,6 +307,27 @@ def gproj(values, steps, stream=None):
     return out[:, :count]
 
 
+def partition(rows, direction: int = MIN, cfg: PlanCfg | None = None, stream=None):
+    """Partition numbers, tile order and tile minima of a candidate set (Sec. 3.1).
+
+    rows: (n, d) uint32 CUDA tensor (int32 bits) or numpy array. Returns CUDA
+    tensors (part int64 [n], order int32 [n] (uint32 bits), tile_min int32
+    [ceil(n/32), d] (uint32 bits)) once queued on the stream."""
+    torch = _torch()
+    r = rows if hasattr(rows, "data_ptr") else to_device_u32(rows)
+    n, d = int(r.shape[0]), int(r.shape[1])
+    dev = r.device
+    ws = alloc_workspace(n, d, 1)
+    part = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    tiles = (n + 31) // 32
+    tmin = torch.empty((max(tiles, 1), d), dtype=torch.int32, device=dev)
+    cfgp = ctypes.byref(cfg) if cfg is not None else None
+    _check(load().gres_partition(_ptr(r), n, d, int(direction), cfgp, _ptr(ws.tensor), ws.nbytes,
+                                 _ptr(part), _ptr(order), _ptr(tmin), _stream_ptr(stream)))
+    return part[:n], order[:n], tmin[:tiles]
+
+
 # ---- resident datasets and queries ---------------------------------------------------
 
 class Dataset:
@@ -401,11 +424,13 @@ class Server:
     """A gres query server (resident datasets, continuous batching) on the current GPU."""
 
     def __init__(self, hbm_budget_bytes: int, max_batch: int = 0, max_inflight: int = 0,
-                 queue_capacity: int = 0, max_k: int = 0, start_paused: bool = False):
+                 queue_capacity: int = 0, max_k: int = 0, start_paused: bool = False,
+                 chunk_targets: int = 0):
         _torch()
         self._lib = load()
         h = _p()
-        cfg = ServeCfg(max_batch, max_inflight, queue_capacity, max_k, 1 if start_paused else 0)
+        cfg = ServeCfg(max_batch, max_inflight, queue_capacity, max_k, 1 if start_paused else 0,
+                       chunk_targets)
         _check(self._lib.gres_serve_create(int(hbm_budget_bytes), ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self.S = {}

@@ -116,3 +116,20 @@ def test_server_argument_checks_need_no_gpu():
     assert lib.gres_serve_submit(None, 0, steps.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(t)) == 1
     assert lib.gres_serve_poll(None, 1, None, 0, None, None, 0) == 1
     assert lib.gres_serve_destroy(None) == 0
+
+
+def test_partition_argument_checks_need_no_gpu():
+    lib = G.load()
+    fake = ctypes.c_void_p(256)
+    for d, direction, cfg in [(0, 0, None), (9, 0, None), (2, 5, None),
+                              (2, 0, G.PlanCfg(scheme=7)),
+                              (3, 0, G.PlanCfg(scheme=G.PART_SLICED, p=4, slice_dim=3)),
+                              (3, 0, G.PlanCfg(scheme=G.PART_ANGULAR, m=65))]:
+        cfgp = ctypes.byref(cfg) if cfg is not None else None
+        rc = lib.gres_partition(fake, 10, d, direction, cfgp, fake, 1 << 30, fake, fake, fake, None)
+        assert rc == 1, (d, direction)
+    # workspace too small / misaligned
+    rc = lib.gres_partition(fake, 10, 2, 0, None, fake, 16, fake, fake, fake, None)
+    assert rc == 1 and b"workspace" in lib.gres_last_error()
+    rc = lib.gres_partition(fake, 10, 2, 0, None, ctypes.c_void_p(260), 1 << 30, fake, fake, fake, None)
+    assert rc == 1

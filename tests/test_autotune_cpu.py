@@ -1,0 +1,75 @@
+"""Autotuner selection logic on the CPU, with a fake timer (no GPU)."""
+import numpy as np
+
+from paper_2412_02274_gb300 import gres as G
+from paper_2412_02274_gb300.autotune import Autotuner, Candidate, default_candidates, size_class
+
+
+class _Rows:
+    """Stands in for an (n, d) device tensor."""
+    def __init__(self, n, d):
+        self.shape = (n, d)
+
+
+def _fake_timer(log):
+    # time depends on the plan in a class-specific way: for d <= 4 Grid m=2 is
+    # fastest, for larger d no partitioning, slots 4 always slower
+    def run(x, steps, direction, cfg, ws):
+        n, d = x.shape
+        log.append((n, d, cfg.scheme, cfg.m, cfg.slots))
+        base = n * 1e-4
+        if d <= 4:
+            t = base * (1.0 if (cfg.scheme == G.PART_GRID and cfg.m == 2) else 2.0)
+        else:
+            t = base * (1.0 if cfg.scheme == G.PART_NONE else 1.5)
+        return t * (1.3 if cfg.slots == 4 else 1.0)
+    return run
+
+
+def test_size_classes():
+    assert size_class(0, 3) == (3, 0)
+    assert size_class(1, 3) == (3, 1)
+    assert size_class(1023, 2) == (2, 10) and size_class(1024, 2) == (2, 11)
+
+
+def test_tuner_picks_fastest_per_class_and_falls_back():
+    log = []
+    tuner = Autotuner(timer=_fake_timer(log))
+    probs = [_Rows(1500, 3), _Rows(1800, 3), _Rows(1600, 3), _Rows(100000, 7), _Rows(3000, 3)]
+    table = tuner.tune(probs, np.arange(1, 9, dtype=np.uint32), samples_per_class=2)
+    assert table[size_class(1500, 3)] == "grid-m2-s8"
+    assert table[size_class(100000, 7)] == "none-s8"
+    # two samples timed in the (3, 11) class: the two largest
+    timed = {(n, d) for n, d, *_ in log}
+    assert (1800, 3) in timed and (1600, 3) in timed and (1500, 3) not in timed
+    assert len(log) == len(default_candidates()) * 4
+    cfg = tuner.plan_for(1700, 3)
+    assert cfg.scheme == G.PART_GRID and cfg.m == 2 and cfg.slots == 8
+    # unseen class: nearest tuned class with the same d; unseen d: the default plan
+    assert tuner.plan_for(10**6, 7).scheme == G.PART_NONE
+    assert tuner.plan_for(10, 3).m == 2
+    dflt = tuner.plan_for(5000, 5)
+    assert dflt.scheme == G.PART_GRID and dflt.m == 0 and dflt.slots == 0
+
+
+def test_tuner_json_round_trip():
+    tuner = Autotuner([Candidate("a", G.PART_GRID, m=2), Candidate("b", G.PART_NONE, slots=4)],
+                      timer=lambda x, s, dr, cfg, ws: 1.0 if cfg.scheme == G.PART_NONE else 2.0)
+    tuner.tune([_Rows(5000, 4)], np.array([1, 2], np.uint32))
+    back = Autotuner.from_json(tuner.to_json())
+    assert back.table == tuner.table == {(4, 13): "b"}
+    cfg = back.plan_for(6000, 4)
+    assert cfg.scheme == G.PART_NONE and cfg.slots == 4
+
+
+def test_batch_objective_weights_the_shared_dominance_launch():
+    # alone, "none" wins (no partitioning cost); in a batch the partitioning of many
+    # instances overlaps and the grid plan's cheaper dominance stage wins
+    def timer(x, steps, direction, cfg, ws):
+        if cfg.scheme == G.PART_NONE:
+            return {"total": 1.0, "skyline": 0.5, "partition": 0.0, "dominance": 0.5}
+        return {"total": 1.2, "skyline": 0.5, "partition": 0.4, "dominance": 0.3}
+    cands = [Candidate("grid", G.PART_GRID, m=2), Candidate("none", G.PART_NONE)]
+    alone = Autotuner(cands, timer=timer).tune([_Rows(5000, 4)], np.array([1, 2], np.uint32))
+    batch = Autotuner(cands, timer=timer, objective="batch").tune([_Rows(5000, 4)], np.array([1, 2], np.uint32))
+    assert alone[(4, 13)] == "none" and batch[(4, 13)] == "grid"

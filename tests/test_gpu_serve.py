@@ -5,6 +5,8 @@ integer and each target is computed independently of the others). Failure
 paths are made on the host: a full queue, a wait that runs out, a cancelled
 query, an HBM budget that is too small.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -96,3 +98,54 @@ def test_hbm_budget():
     np.testing.assert_array_equal(got, G.Dataset(small).query(steps_log(100, 16)).cpu().numpy())
     assert sv.stats()["device_bytes"] <= budget
     sv.close()
+
+
+def test_queries_in_pieces():
+    """Queries split into pieces of a few hundred targets give the same results; a query
+    on a small skyline submitted after one on a large skyline finishes first."""
+    rng = np.random.default_rng(7)
+    dsets = _datasets()
+    alone = [G.Dataset(data, direction, cfg) for data, direction, cfg in dsets]
+    for chunk in (300, -1):
+        sv = G.Server(8 << 30, max_batch=16, max_inflight=3, chunk_targets=chunk)
+        ids = [sv.add_dataset(data, direction, cfg) for data, direction, cfg in dsets]
+        queries = [(int(rng.integers(0, len(ids))), steps_log(int(rng.integers(64, 257)), 16)) for _ in range(60)]
+        tickets = [sv.submit(ids[j], steps) for j, steps in queries]
+        for t, (j, steps) in zip(tickets, queries):
+            got, _ = sv.poll(t)
+            np.testing.assert_array_equal(got, alone[j].query(steps).cpu().numpy())
+        sv.close()
+    # ordering: the largest skyline in many pieces, then the smallest
+    sizes = [ds.S for ds in alone]
+    big, small = int(np.argmax(sizes)), int(np.argmin(sizes))
+    assert sizes[big] > 20 * 100
+    sv = G.Server(8 << 30, max_batch=16, max_inflight=2, chunk_targets=100, start_paused=True)
+    ids = [sv.add_dataset(data, direction, cfg) for data, direction, cfg in dsets]
+    steps = steps_log(256, 16)
+    tb = sv.submit(ids[big], steps)
+    ts = sv.submit(ids[small], steps)
+    sv.resume()
+    got_s, lat_s = sv.poll(ts)
+    got_b, lat_b = sv.poll(tb)
+    assert lat_s < lat_b
+    np.testing.assert_array_equal(got_b, alone[big].query(steps).cpu().numpy())
+    np.testing.assert_array_equal(got_s, alone[small].query(steps).cpu().numpy())
+    # a cancelled query in pieces ends cleanly: the dataset can be removed afterwards
+    tc = sv.submit(ids[big], steps)
+    sv.cancel(tc)
+    with pytest.raises(G.GresError):
+        sv.poll(tc, timeout_us=0)
+    got, _ = sv.poll(sv.submit(ids[big], steps))
+    np.testing.assert_array_equal(got, alone[big].query(steps).cpu().numpy())
+    for _ in range(1000):
+        try:
+            sv.remove_dataset(ids[big])
+            break
+        except G.GresError as e:
+            assert e.status == EAGAIN
+            time.sleep(0.002)
+    else:
+        raise AssertionError("dataset still busy after its queries ended")
+    sv.close()
+    for ds in alone:
+        ds.close()
