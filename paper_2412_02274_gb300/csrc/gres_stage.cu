@@ -38,7 +38,7 @@
 // first dominated step. The candidate rows and tile minima are staged in
 // shared memory with cp.async when they fit (they do for skylines up to
 // about 6,900 rows at d = 6), otherwise read through L1.
-#include "gres_internal.cuh"
+#include "cluster.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -171,6 +171,58 @@ __device__ __forceinline__ unsigned long long morton16(const uint32_t (&x)[D], c
 //   SLICED:  first pass keys on x_dim; the slice comes from the rank.
 // Sort key = partition << 16 | morton16 (order inside a partition), value = row.
 template <int D>
+__device__ __forceinline__ unsigned long long part_key(const uint32_t *sky_rows, long long j, const WsHeader *h,
+                                                       const PartArgs &a) {
+    uint32_t x[D];
+    ld_row<D>(sky_rows, j, x);
+    #pragma unroll
+    for (int i = 0; i < D; i++) x[i] -= h->lo[i];
+    unsigned long long pid = 0;
+    if (a.scheme == GRES_PART_GRID) {
+        unsigned long long w = 1;
+        #pragma unroll
+        for (int i = 0; i < D; i++) {
+            const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
+            pid += ((unsigned long long)x[i] * (unsigned long long)a.m) / span * w;
+            w *= (unsigned long long)a.m;
+        }
+        return (pid << 16) | morton16<D>(x, h);
+    }
+    if (a.scheme == GRES_PART_ANGULAR) {
+        unsigned long long w = 1;
+        #pragma unroll
+        for (int i = 0; i + 1 < D; i++) {
+            const unsigned __int128 X = (unsigned __int128)x[i] * x[i];
+            unsigned __int128 Y = 0;
+            #pragma unroll
+            for (int q = i + 1; q < D; q++) Y += (unsigned __int128)x[q] * x[q];
+            int bin = 0;
+            if (!(X == 0 && Y == 0)) {
+                for (int t = 1; t < a.m; t++)
+                    if ((Y << 32) >= X * (unsigned __int128)a.thr[t]) bin = t;
+            }
+            pid += (unsigned long long)bin * w;
+            w *= (unsigned long long)a.m;
+        }
+        return (pid << 16) | morton16<D>(x, h);
+    }
+    return pick<D>(x, a.dim);   // SLICED, first pass
+}
+
+// SLICED second pass key of the row of rank r (its row j read from the
+// sorted values): slice floor(r p / S) << 16 | morton16.
+template <int D>
+__device__ __forceinline__ unsigned long long sliced_key(const uint32_t *sky_rows, uint32_t j, long long r,
+                                                         long long S, const WsHeader *h, const PartArgs &a) {
+    uint32_t x[D];
+    ld_row<D>(sky_rows, j, x);
+    const unsigned long long slice = (unsigned long long)r * (unsigned long long)a.p / (unsigned long long)S;
+    #pragma unroll
+    for (int q = 0; q < D; q++) x[q] -= h->lo[q];
+    return (slice << 16) | morton16<D>(x, h);
+}
+
+template <int D>
 __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
                             unsigned long long *keys, uint32_t *vals) {
     const long long S = h->n_sky;
@@ -182,42 +234,7 @@ __global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
         unsigned long long key = 0;
         const bool valid = j < S;
         if (valid) {
-            uint32_t x[D];
-            ld_row<D>(sky_rows, j, x);
-            #pragma unroll
-            for (int i = 0; i < D; i++) x[i] -= h->lo[i];
-            unsigned long long pid = 0;
-            if (a.scheme == GRES_PART_GRID) {
-                unsigned long long w = 1;
-                #pragma unroll
-                for (int i = 0; i < D; i++) {
-                    const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
-                    pid += ((unsigned long long)x[i] * (unsigned long long)a.m) / span * w;
-                    w *= (unsigned long long)a.m;
-                }
-                key = (pid << 16) | morton16<D>(x, h);
-            } else if (a.scheme == GRES_PART_ANGULAR) {
-                unsigned long long w = 1;
-                #pragma unroll
-                for (int i = 0; i + 1 < D; i++) {
-                    const unsigned __int128 X = (unsigned __int128)x[i] * x[i];
-                    unsigned __int128 Y = 0;
-                    #pragma unroll
-                    for (int q = i + 1; q < D; q++) Y += (unsigned __int128)x[q] * x[q];
-                    int bin = 0;
-                    if (!(X == 0 && Y == 0)) {
-                        for (int t = 1; t < a.m; t++)
-                            if ((Y << 32) >= X * (unsigned __int128)a.thr[t]) bin = t;
-                    }
-                    pid += (unsigned long long)bin * w;
-                    w *= (unsigned long long)a.m;
-                }
-                key = (pid << 16) | morton16<D>(x, h);
-            } else {  // SLICED, first pass
-                key = pick<D>(x, a.dim);
-            }
-        }
-        if (valid) {
+            key = part_key<D>(sky_rows, j, h, a);
             keys[j] = key;
             vals[j] = (uint32_t)j;
         }
@@ -242,14 +259,7 @@ __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
         const bool valid = r < S;
         if (valid) {
             j = vals[r];
-            uint32_t x[D];
-            ld_row<D>(sky_rows, j, x);
-            const unsigned long long slice =
-                (unsigned long long)r * (unsigned long long)a.p / (unsigned long long)S;
-            uint32_t xr[D];
-            #pragma unroll
-            for (int q = 0; q < D; q++) xr[q] = x[q] - h->lo[q];
-            key = (slice << 16) | morton16<D>(xr, h);
+            key = sliced_key<D>(sky_rows, j, r, S, h, a);
         }
         if (valid) {
             keys0[r] = key;
@@ -263,20 +273,16 @@ __global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
 // sentinel rows (all ones: never dominate), each tile's per-attribute minimum
 // (tmin) and each 1024-row super-tile's minimum (smin). One block of 1024
 // threads per super-tile; warp w builds tile w of it.
+// Super-tile sup of the candidate layout, by one 1024-thread block; warp w
+// builds tile w of it. wm: 32 x DP words of shared memory.
 template <int D>
-__global__ void __launch_bounds__(1024)
-k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1,
-          const WsHeader *h, int identity, uint32_t *cand, uint32_t *tmin, uint32_t *smin,
-          uint32_t *perm) {
+__device__ __forceinline__ void permute_super(const uint32_t *sky_rows, const uint32_t *vals, int identity,
+                                              long long S, long long sup, uint32_t *cand, uint32_t *tmin,
+                                              uint32_t *smin, uint32_t *perm, uint32_t (*wm)[padded_dims(D)]) {
     constexpr int DP = padded_dims(D);
-    const long long S = h->n_sky;
     const long long T = (S + kTileRows - 1) / kTileRows;
-    const long long T2 = (T + 31) / 32;
-    if ((long long)blockIdx.x >= T2) return;
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    __shared__ uint32_t wm[32][DP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long tile = (long long)blockIdx.x * 32 + w;
+    const long long tile = sup * 32 + w;
     const long long i = tile * kTileRows + lane;
     uint32_t x[DP];
     if (i < S) {
@@ -312,9 +318,93 @@ k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1
             uint32_t v = wm[lane][q];
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
-            if (lane == 0) smin[(long long)blockIdx.x * DP + q] = v;
+            if (lane == 0) smin[sup * DP + q] = v;
         }
     }
+    __syncthreads();
+}
+
+template <int D>
+__global__ void __launch_bounds__(1024)
+k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1,
+          const WsHeader *h, int identity, uint32_t *cand, uint32_t *tmin, uint32_t *smin,
+          uint32_t *perm) {
+    constexpr int DP = padded_dims(D);
+    const long long S = h->n_sky;
+    const long long T = (S + kTileRows - 1) / kTileRows;
+    const long long T2 = (T + 31) / 32;
+    if ((long long)blockIdx.x >= T2) return;
+    __shared__ uint32_t wm[32][DP];
+    permute_super<D>(sky_rows, h->sorted_sel ? vals1 : vals0, identity, S, (long long)blockIdx.x, cand, tmin,
+                     smin, perm, wm);
+}
+
+// The whole partitioning of a skyline of S rows as one cluster launch: keys,
+// the stable sort (two for SLICED: by the chosen attribute, then by slice and
+// Morton code), and the candidate layout -- what k_part_keys, the radix sorts,
+// k_sliced_keys and k_permute compute.
+template <int D>
+__global__ void __launch_bounds__(kClThreads)
+k_part_cluster(const uint32_t *sky_rows, WsHeader *h, PartArgs a, unsigned long long *k0, uint32_t *v0,
+               unsigned long long *k1, uint32_t *v1, uint32_t *cand, uint32_t *tmin, uint32_t *smin,
+               uint32_t *perm) {
+    constexpr int DP = padded_dims(D);
+    extern __shared__ uint32_t sm[];
+    __shared__ unsigned long long kr[2];
+    __shared__ uint32_t wm[32][DP];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const long long tt = (long long)C * kClThreads, gt = (long long)r * kClThreads + threadIdx.x;
+    const long long S = h->n_sky;
+    const bool none = a.scheme == GRES_PART_NONE;
+    int sel = 0;
+    if (!none) {
+        // first key: partition number << 16 | Morton code (SLICED: the chosen attribute)
+        if (threadIdx.x == 0) { kr[0] = ~0ull; kr[1] = 0ull; }
+        __syncthreads();
+        unsigned long long kmn = ~0ull, kmx = 0ull;
+        for (long long j = gt; j < S; j += tt) {
+            const unsigned long long key = part_key<D>(sky_rows, j, h, a);
+            k0[j] = key;
+            v0[j] = (uint32_t)j;
+            kmn = key < kmn ? key : kmn;
+            kmx = key > kmx ? key : kmx;
+        }
+        cta_key_add(kmn, kmx, kr);
+        unsigned long long kmin, kmax;
+        cluster_key_range(cl, kr, &kmin, &kmax);
+        int passes = key_passes(kmin, kmax);
+        cluster_radix_sort(cl, sm, k0, v0, k1, v1, S, kmin, passes);
+        sel = passes & 1;
+        if (a.scheme == GRES_PART_SLICED) {
+            // rank r -> slice floor(r p / S); re-key in place into buffer 0, sort again
+            const uint32_t *vs = sel ? v1 : v0;
+            __shared__ unsigned long long kr2[2];
+            if (threadIdx.x == 0) { kr2[0] = ~0ull; kr2[1] = 0ull; }
+            __syncthreads();
+            kmn = ~0ull;
+            kmx = 0ull;
+            for (long long q = gt; q < S; q += tt) {
+                const uint32_t j = vs[q];
+                const unsigned long long key = sliced_key<D>(sky_rows, j, q, S, h, a);
+                k0[q] = key;
+                v0[q] = j;
+                kmn = key < kmn ? key : kmn;
+                kmx = key > kmx ? key : kmx;
+            }
+            cta_key_add(kmn, kmx, kr2);
+            cluster_key_range(cl, kr2, &kmin, &kmax);
+            passes = key_passes(kmin, kmax);
+            cluster_radix_sort(cl, sm, k0, v0, k1, v1, S, kmin, passes);
+            sel = passes & 1;
+        }
+    }
+    const long long T = (S + kTileRows - 1) / kTileRows;
+    const long long T2 = (T + 31) / 32;
+    for (long long sup = r; sup < T2; sup += C)
+        permute_super<D>(sky_rows, sel ? v1 : v0, none ? 1 : 0, S, sup, cand, tmin, smin, perm, wm);
+    if (r == 0 && threadIdx.x == 0) h->sorted_sel = (unsigned)sel;
+    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // gres_partition: the caller's rows, canonical and padded, as the candidate
@@ -387,8 +477,13 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 
-template <int D>
-__host__ __device__ constexpr int dom_threads() { return D <= 4 ? 512 : (D <= 6 ? 384 : 256); }
+// Threads per block of the grid-dominance kernels (one block per SM): as many
+// warps as the per-thread registers of each (D, SLOTS) leave room for.
+template <int D, int SLOTS>
+__host__ __device__ constexpr int dom_threads() {
+    return SLOTS == 8 ? (D <= 2 ? 640 : D <= 4 ? 512 : D <= 6 ? 384 : 256)
+                      : (D <= 2 ? 768 : D <= 3 ? 640 : D <= 4 ? 576 : D <= 6 ? 512 : 384);
+}
 
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
@@ -560,7 +655,7 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
 }
 
 template <int D, int SLOTS>
-__global__ void __launch_bounds__(dom_threads<D>(), 1)
+__global__ void __launch_bounds__(dom_threads<D, SLOTS>(), 1)
 k_dominance(DomArgs a) {
     constexpr int DP = padded_dims(D);
     constexpr int WS = 32 * SLOTS;
@@ -626,7 +721,7 @@ struct DomBatch {
 };
 
 template <int D, int SLOTS>
-__global__ void __launch_bounds__(dom_threads<D>(), 1)
+__global__ void __launch_bounds__(dom_threads<D, SLOTS>(), 1)
 k_dominance_batch(const __grid_constant__ DomBatch b) {
     constexpr int WS = 32 * SLOTS;
     __shared__ unsigned long long first[kMaxBatch + 1];   // prefix sums of the targets
@@ -728,14 +823,14 @@ cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
         configured = true;
     }
     a.smem_words = smem / 4;
-    k_dominance<D, SLOTS><<<g_sm_count, dom_threads<D>(), smem, st>>>(a); note_launch();
+    k_dominance<D, SLOTS><<<g_sm_count, dom_threads<D, SLOTS>(), smem, st>>>(a); note_launch();
     return cudaGetLastError();
 }
 
 template <int D, int SLOTS>
 cudaError_t launch_dom_batch(const DomBatch &b, cudaStream_t st) {
-    const int smem = (dom_threads<D>() / 32) * 32 * SLOTS * 4;
-    k_dominance_batch<D, SLOTS><<<g_sm_count, dom_threads<D>(), smem, st>>>(b); note_launch();
+    const int smem = (dom_threads<D, SLOTS>() / 32) * 32 * SLOTS * 4;
+    k_dominance_batch<D, SLOTS><<<g_sm_count, dom_threads<D, SLOTS>(), smem, st>>>(b); note_launch();
     return cudaGetLastError();
 }
 
@@ -763,6 +858,12 @@ cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cuda
     if (scheme == GRES_PART_GRID || scheme == GRES_PART_ANGULAR)
         for (int i = 0; i < (scheme == GRES_PART_GRID ? D : D - 1); i++) cells *= (unsigned long long)cfg.m;
     cudaError_t e;
+    if (n <= kClusterSortMax) {
+        static bool configured = false;
+        return launch_cluster(k_part_cluster<D>, kClSortBytes, &configured, st, (const uint32_t *)ws.sky_rows,
+                              ws.hdr, pa, ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], ws.cand, ws.tmin,
+                              ws.smin, ws.perm);
+    }
     if (scheme != GRES_PART_NONE) {
         k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]); note_launch();
         const int bits1 = scheme == GRES_PART_SLICED ? 32 : 16 + bits_of(cells - 1);

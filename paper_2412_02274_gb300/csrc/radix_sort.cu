@@ -14,11 +14,7 @@
 // ranks its items per digit in input order (warp match_any for ranks within a
 // warp, a per-digit prefix over warps for the block, a running per-digit carry
 // across the block's rounds).
-#include "gres_internal.cuh"
-
-#include <cooperative_groups.h>
-
-namespace cg = cooperative_groups;
+#include "cluster.cuh"
 
 namespace gres {
 
@@ -178,112 +174,17 @@ k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_i
 }
 
 // ---- one-launch sort for small inputs: one thread-block cluster -------------
-// All passes in one launch of kSortCluster CTAs. CTA r owns the contiguous
-// range [r c, (r + 1) c) of the input (c = ceil(n / C) rounded up to 32), so
-// stability only needs ranks in index order inside each CTA. A pass: each CTA
-// histograms its range in shared memory; after a cluster barrier every CTA
-// reads the C histograms through distributed shared memory and takes, for
-// each digit, the items of all smaller digits plus the items of its digit in
-// lower-ranked CTAs as its base; then it scatters its range in rounds of
-// kSortThreads items (ranks as in k_scatter); a second cluster barrier makes
-// the scattered data visible to the next pass. The barriers are the hardware
-// cluster barrier (release / acquire at cluster scope): nothing spins.
-constexpr int kSortCluster = 8;
-constexpr int kSortThreads = 1024;
-constexpr int kSortWarps = kSortThreads / 32;
-
-__global__ void __launch_bounds__(kSortThreads)
+// All passes in one launch (cluster_radix_sort, cluster.cuh); the pass count
+// comes from the device-side key range as in the three-kernel form.
+__global__ void __launch_bounds__(kClThreads)
 k_sort_cluster(WsHeader *h, unsigned long long *k0, uint32_t *v0, unsigned long long *k1, uint32_t *v1,
                const long long *d_n, int max_passes) {
     extern __shared__ uint32_t sm[];
-    uint32_t *hist = sm;                      // 256: this CTA's digit counts (read by the cluster)
-    uint32_t *base = sm + 256;                // 256: running scatter base per digit
-    uint32_t *wsum = sm + 512;                // kSortWarps
-    uint32_t *wcnt = sm + 512 + kSortWarps;   // kSortWarps x 256
-    uint32_t *woff = wcnt + kSortWarps * 256; // kSortWarps x 256
     cg::cluster_group cl = cg::this_cluster();
-    const int C = (int)cl.num_blocks();
-    const int r = (int)cl.block_rank();
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int all = radix_passes(h);
-    const int passes = all < max_passes ? all : max_passes;
-    if (r == 0 && tid == 0) h->sorted_sel = (unsigned)(all & 1);
-    const long long n = *d_n;
-    const long long chunk = (((n + C - 1) / C) + 31) & ~31LL;
-    const long long b0 = min(n, (long long)r * chunk), b1 = min(n, b0 + chunk);
-    const unsigned long long kmin = h->key_min;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (int pass = 0; pass < passes; pass++) {
-        const unsigned long long *kin = (pass & 1) ? k1 : k0;
-        const uint32_t *vin = (pass & 1) ? v1 : v0;
-        unsigned long long *kout = (pass & 1) ? k0 : k1;
-        uint32_t *vout = (pass & 1) ? v0 : v1;
-        const int shift = 8 * pass;
-        if (tid < 256) hist[tid] = 0;
-        for (int j = tid; j < kSortWarps * 256; j += kSortThreads) wcnt[j] = 0;
-        __syncthreads();
-        for (long long i = b0 + tid; i < b1; i += kSortThreads)
-            atomicAdd(&hist[(uint32_t)(((kin[i] - kmin) >> shift) & 255ull)], 1u);
-        cl.sync();
-        if (tid < 256) {
-            uint32_t tot = 0, pre = 0;
-            for (int q = 0; q < C; q++) {
-                const uint32_t c = cl.map_shared_rank(hist, q)[tid];
-                tot += c;
-                pre += q < r ? c : 0u;
-            }
-            uint32_t incl = tot;
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane == 31) wsum[w] = incl;
-            asm volatile("bar.sync 1, 256;" ::: "memory");
-            uint32_t before = 0;
-            #pragma unroll
-            for (int j = 0; j < 8; j++) before += j < w ? wsum[j] : 0u;
-            base[tid] = before + incl - tot + pre;
-        }
-        __syncthreads();
-        for (long long r0 = b0; r0 < b1; r0 += kSortThreads) {
-            const long long i = r0 + tid;
-            const bool valid = i < b1;
-            unsigned long long key = 0;
-            uint32_t val = 0;
-            uint32_t dg = 256;  // invalid items share a digit no real item has
-            if (valid) {
-                key = kin[i];
-                val = vin[i];
-                dg = (uint32_t)(((key - kmin) >> shift) & 255ull);
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, dg);
-            const uint32_t rank = __popc(peers & lt_mask);
-            if (valid && rank == 0) wcnt[w * 256 + dg] = __popc(peers);
-            __syncthreads();
-            if (tid < 256) {
-                uint32_t run = base[tid];
-                #pragma unroll 8
-                for (int j = 0; j < kSortWarps; j++) {
-                    const uint32_t c = wcnt[j * 256 + tid];
-                    wcnt[j * 256 + tid] = 0;
-                    woff[j * 256 + tid] = run;
-                    run += c;
-                }
-                base[tid] = run;
-            }
-            __syncthreads();
-            if (valid) {
-                const uint32_t pos = woff[w * 256 + dg] + rank;
-                kout[pos] = key;
-                vout[pos] = val;
-            }
-        }
-        cl.sync();
-    }
+    if (cl.block_rank() == 0 && threadIdx.x == 0) h->sorted_sel = (unsigned)(all & 1);
+    cluster_radix_sort(cl, sm, k0, v0, k1, v1, *d_n, h->key_min, all < max_passes ? all : max_passes);
 }
-
-constexpr size_t kSortSmem = sizeof(uint32_t) * (512 + kSortWarps + 2 * kSortWarps * 256);
 
 }  // namespace
 
@@ -291,28 +192,8 @@ int64_t sort_blocks(int64_t n) { return (n + kTile - 1) / kTile; }
 
 cudaError_t launch_sort_cluster(Workspace &ws, const long long *d_n, int max_passes, cudaStream_t st) {
     static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_sort_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSortSmem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kSortCluster, 1, 1);
-    cfg.blockDim = dim3(kSortThreads, 1, 1);
-    cfg.dynamicSmemBytes = kSortSmem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kSortCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_sort_cluster, ws.hdr, ws.keys[0], ws.vals[0], ws.keys[1],
-                                       ws.vals[1], d_n, max_passes);
-    note_launch();
-    return e;
+    return launch_cluster(k_sort_cluster, kClSortBytes, &configured, st, ws.hdr, ws.keys[0], ws.vals[0],
+                          ws.keys[1], ws.vals[1], d_n, max_passes);
 }
 
 // Queues up to `max_passes` digit passes on ws.keys[0]/ws.vals[0] (count in

@@ -19,7 +19,7 @@
 //               dominates it, and skyline tuples always survive step 3.)
 //   6. flags by original row -> ascending row numbers, plus the canonical
 //      skyline rows for the gres stage.
-#include "gres_internal.cuh"
+#include "cluster.cuh"
 
 #include <algorithm>
 
@@ -334,9 +334,12 @@ __device__ __forceinline__ void rep_compact(uint32_t *rows, const uint32_t *rep_
 constexpr int kRepBlock = 1024;
 template <int D>
 __global__ void __launch_bounds__(kRepBlock)
-k_rep_flags(uint32_t *cand_rows, WsHeader *h, uint32_t *rep_flag) {
+k_rep_flags(uint32_t *cand_rows, WsHeader *h, uint32_t *rep_flag, uint32_t *blocksum, long long nb) {
     __shared__ uint32_t rows[D * kMaxReps];
     const int nc = (int)h->n_cand;
+    // the filter's per-segment survivor counts start at zero
+    for (long long j = (long long)blockIdx.x * kRepBlock + threadIdx.x; j < nb; j += (long long)gridDim.x * kRepBlock)
+        blocksum[j] = 0u;
     for (int i = threadIdx.x; i < nc; i += kRepBlock) {
         uint32_t x[D];
         load_row<D>(cand_rows, i, x);
@@ -368,20 +371,25 @@ k_rep_flags(uint32_t *cand_rows, WsHeader *h, uint32_t *rep_flag) {
 }
 
 // Survivor flags (not dominated by any representative), rows in input order,
-// plus per-block counts for the compaction. The representatives sit in shared
-// memory (attribute-major) in runs of 32 with each run's per-attribute
-// minimum; a run can hold a dominator of x only if its minimum is <= x in
-// every attribute. Each warp loads 32 rows (one per lane) and takes them one
-// at a time: lanes first test the runs' minima, then the rows of each
-// possible run, stopping at the first dominator.
-constexpr int kFilterThreads = kCB;   // one warp per 32 rows of the block's kCB rows
+// plus per-segment survivor counts (kCB-row segments) for the compaction. The
+// representatives sit in shared memory (attribute-major) in runs of 32 with
+// each run's per-attribute minimum; a run can hold a dominator of x only if
+// its minimum is <= x in every attribute. Each lane keeps the minimum of run
+// `lane` in registers. A warp takes kFilterRowsPerWarp rows and checks them
+// one at a time: the lanes test the run minima, then the rows of each
+// possible run, stopping at the first dominator. Blocks stay resident and
+// step through kFilterChunk-row chunks, so the representatives are staged
+// once per block and short per-warp chains keep many warps in flight.
+constexpr int kFilterThreads = 512;
+constexpr int kFilterRowsPerWarp = 4;
+constexpr int kFilterChunk = (kFilterThreads / 32) * kFilterRowsPerWarp;
+static_assert(kCB % kFilterChunk == 0, "a chunk lies inside one compaction segment");
 template <int D>
 __global__ void __launch_bounds__(kFilterThreads)
 k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHeader *h,
          uint32_t *flags, uint32_t *blocksum, long long nb) {
     __shared__ uint32_t rs[D * kMaxReps];
     __shared__ uint32_t rmin[D * (kMaxReps / 32)];
-    __shared__ uint32_t cnt;
     const int nr = (int)h->n_reps;
     const int nruns = (nr + 31) / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -401,28 +409,29 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
             if ((j & 31) == 0) rmin[q * (kMaxReps / 32) + (j >> 5)] = m;
         }
     }
-    if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    const long long b0 = (long long)blockIdx.x * kCB;
-    uint32_t mine = 0;
-    for (int g = warp; g < kCB / 32; g += kFilterThreads / 32) {
-        const long long p = b0 + g * 32 + lane;
+    uint32_t mn[D];   // minimum of run `lane`
+    #pragma unroll
+    for (int q = 0; q < D; q++) mn[q] = lane < nruns ? rmin[q * (kMaxReps / 32) + lane] : 0xFFFFFFFFu;
+    const bool run_ok = lane < nruns;
+    for (long long c0 = (long long)blockIdx.x * kFilterChunk; c0 < n; c0 += (long long)gridDim.x * kFilterChunk) {
+        const long long g0 = c0 + (long long)warp * kFilterRowsPerWarp;
+        if (g0 >= n) continue;
+        const int lim = (int)min((long long)kFilterRowsPerWarp, n - g0);
         uint32_t x[D];
-        if (p < n) load_canon<D>(data, p, dir, x);
+        if (lane < lim) load_canon<D>(data, g0 + lane, dir, x);
         else {
             #pragma unroll
             for (int q = 0; q < D; q++) x[q] = 0u;
         }
         unsigned alive_mask = 0;
-        const int lim = (int)min(32LL, n - (b0 + g * 32));
         for (int l = 0; l < lim; l++) {
             uint32_t xs[D];
             #pragma unroll
             for (int q = 0; q < D; q++) xs[q] = __shfl_sync(0xffffffffu, x[q], l);
-            // runs whose minimum is <= xs everywhere (lane = run)
-            bool maybe = lane < nruns;
+            bool maybe = run_ok;
             #pragma unroll
-            for (int q = 0; q < D; q++) maybe &= lane < nruns && rmin[q * (kMaxReps / 32) + lane] <= xs[q];
+            for (int q = 0; q < D; q++) maybe &= mn[q] <= xs[q];
             unsigned runs = __ballot_sync(0xffffffffu, maybe);
             bool dom = false;
             while (runs && !dom) {
@@ -436,17 +445,9 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
             }
             if (!dom) alive_mask |= 1u << l;
         }
-        if (p < n) {
-            const bool alive = (alive_mask >> lane) & 1u;
-            flags[p] = alive ? 1u : 0u;
-            mine += alive ? 1u : 0u;
-        }
+        if (lane < lim) flags[g0 + lane] = (alive_mask >> lane) & 1u;
+        if (lane == 0 && alive_mask) atomicAdd(&blocksum[g0 / kCB], (uint32_t)__popc(alive_mask));
     }
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    if (lane == 0 && mine) atomicAdd(&cnt, mine);
-    __syncthreads();
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = cnt;
     if (last_block_done(&h->done[2])) {
         // survivors' offsets; the sort-key range is cleared for the survivor sort
         const uint32_t total = block_scan_inplace(blocksum, nb);
@@ -459,11 +460,12 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
 }
 
 // Survivors in input order: canonical rows, original row numbers, and their
-// per-attribute range (slo / shi) for the spatial order.
+// per-attribute range (slo / shi) for the spatial order. With `clear`, the
+// flags read are reset to 0 for k_final.
 template <int D>
 __global__ void __launch_bounds__(kCT)
-k_compact_surv(const uint32_t *data, int dir, long long n, const uint32_t *flags, const uint32_t *blocksum,
-               uint32_t *surv_rows, uint32_t *surv_orig, WsHeader *h) {
+k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, const uint32_t *blocksum,
+               uint32_t *surv_rows, uint32_t *surv_orig, WsHeader *h, int clear) {
     __shared__ uint32_t blo[D], bhi[D];
     if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
     uint32_t run = blocksum[blockIdx.x];
@@ -475,6 +477,7 @@ k_compact_surv(const uint32_t *data, int dir, long long n, const uint32_t *flags
     for (int r = 0; r < kPer; r++) {
         const long long p = b0 + r * kCT + threadIdx.x;
         const uint32_t f = p < n ? flags[p] : 0u;
+        if (clear && f) flags[p] = 0u;   // cleared for k_final
         uint32_t tot;
         const uint32_t ex = block_scan(f, &tot);
         if (f) {
@@ -708,6 +711,97 @@ k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyfla
     }
 }
 
+// ---- the survivor sort as a single cluster launch ------------------------
+// For inputs of at most kClusterSortMax rows the O(survivors) stages between
+// the survivor compaction and the final check run as one cluster launch
+// (cluster.cuh) instead of a chain of small kernels, computing exactly what
+// the chain computes. The O(n) compactions stay grid-wide.
+
+// The survivors' 16-bit Morton keys over their range, the stable sort by
+// key, and the survivor tiles in that order (rows, original row numbers, tile
+// and super-tile minima) -- the work of k_surv_keys, the radix sort and
+// k_gather_tiles, for the M survivors k_compact_surv left.
+template <int D>
+__global__ void __launch_bounds__(kClThreads)
+k_surv_cluster(Workspace ws) {
+    constexpr int DP = padded_dims(D);
+    extern __shared__ uint32_t sm[];
+    __shared__ unsigned long long kr[2];
+    __shared__ uint32_t wm[32][DP];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long tt = (long long)C * kClThreads, gt = (long long)r * kClThreads + tid;
+    WsHeader *h = ws.hdr;
+    const long long M = h->n_surv;
+    if (tid == 0) { kr[0] = ~0ull; kr[1] = 0ull; }
+    __syncthreads();
+    const int bits = 16 / D;
+    unsigned long long kmn = ~0ull, kmx = 0ull;
+    for (long long j = gt; j < M; j += tt) {
+        uint32_t x[D];
+        load_row<D>(ws.surv_rows, j, x);
+        const unsigned long long k = morton<D>(x, h->slo, h->shi, bits);
+        ws.keys[0][j] = k;
+        ws.vals[0][j] = (uint32_t)j;
+        kmn = k < kmn ? k : kmn;
+        kmx = k > kmx ? k : kmx;
+    }
+    cta_key_add(kmn, kmx, kr);
+    unsigned long long kmin, kmax;
+    cluster_key_range(cl, kr, &kmin, &kmax);
+    const int passes = key_passes(kmin, kmax);
+    cluster_radix_sort(cl, sm, ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], M, kmin, passes);
+    const uint32_t *vals = ws.vals[passes & 1];
+    // survivor tiles in key order: one super-tile per CTA and round, warp w builds its tile w
+    const long long T = (M + kTileRows - 1) / kTileRows;
+    const long long T2 = (T + 31) / 32;
+    for (long long sup = r; sup < T2; sup += C) {
+        const long long tile = sup * 32 + w;
+        const long long row = tile * kTileRows + lane;
+        uint32_t x[DP];
+        if (row < M) {
+            const uint32_t j = vals[row];
+            const uint4 *src = reinterpret_cast<const uint4 *>(ws.surv_rows + (long long)j * DP);
+            const uint4 a = src[0];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            if (DP == 8) { const uint4 b = src[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
+            ws.perm[row] = ws.surv_orig[j];
+        } else {
+            #pragma unroll
+            for (int q = 0; q < DP; q++) x[q] = kSentinel;
+        }
+        if (tile < T) {
+            uint4 *dst = reinterpret_cast<uint4 *>(ws.cand + row * DP);
+            dst[0] = make_uint4(x[0], x[1], x[2], x[3]);
+            if (DP == 8) dst[1] = make_uint4(x[4 % DP], x[5 % DP], x[6 % DP], x[7 % DP]);
+        }
+        #pragma unroll
+        for (int q = 0; q < DP; q++) {
+            uint32_t m = x[q];
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) {
+                wm[w][q] = m;
+                if (tile < T) ws.tmin[tile * DP + q] = m;
+            }
+        }
+        __syncthreads();
+        if (w == 0) {
+            #pragma unroll
+            for (int q = 0; q < DP; q++) {
+                uint32_t m = wm[lane][q];
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) ws.smin[sup * DP + q] = m;
+            }
+        }
+        __syncthreads();
+    }
+    if (r == 0 && tid == 0) h->sorted_sel = (unsigned)(passes & 1);
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 template <int D>
 cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Workspace &ws,
                       int64_t *d_sky_idx, cudaStream_t st) {
@@ -722,16 +816,33 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     k_sel_gather<<<gb, 256, 0, st>>>(ws.keys[0], n, ws.hdr, ws.rep_key, ws.rep_idx); note_launch();
     k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps); note_launch();
     const int r_eff = (int)std::min<int64_t>(reps, n);
-    k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(ws.reps, ws.hdr, ws.perm); note_launch();
-    k_filter<D><<<(unsigned)nb, kFilterThreads, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum, nb); note_launch();
+    k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(ws.reps, ws.hdr, ws.perm, ws.blocksum, nb); note_launch();
+    static int filter_blocks = 0;   // resident blocks of k_filter<D> on this GPU
+    if (filter_blocks == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<D>, kFilterThreads, 0);
+        filter_blocks = std::max(1, per_sm) * std::max(1, sms);
+    }
+    const long long fchunks = (n + kFilterChunk - 1) / kFilterChunk;
+    const int fb = (int)std::min<long long>(fchunks, (long long)filter_blocks);
+    k_filter<D><<<fb, kFilterThreads, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum, nb); note_launch();
+    const bool small = n <= kClusterSortMax;
     k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
-                                                     ws.surv_orig, ws.hdr); note_launch();
-    k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
-    e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 2, st);
-    if (e != cudaSuccess) return e;
-    const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
-    k_gather_tiles<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1],
-                                                       ws.hdr, ws.cand, ws.perm, ws.tmin, ws.smin); note_launch();
+                                                     ws.surv_orig, ws.hdr, small ? 1 : 0); note_launch();
+    if (small) {
+        static bool configured = false;
+        e = launch_cluster(k_surv_cluster<D>, kClSortBytes, &configured, st, ws);
+        if (e != cudaSuccess) return e;
+    } else {
+        k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
+        e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 2, st);
+        if (e != cudaSuccess) return e;
+        const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
+        k_gather_tiles<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1],
+                                                           ws.hdr, ws.cand, ws.perm, ws.tmin, ws.smin); note_launch();
+    }
     k_final<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
         ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags); note_launch();
     k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum, nb, ws.hdr); note_launch();

@@ -64,7 +64,8 @@ SCHEMES = [
 @pytest.mark.parametrize("name,mk", SCHEMES, ids=[s[0] for s in SCHEMES])
 def test_partition_numbers_match_oracle(name, mk):
     cases = [("uni", 1, 3), ("uni", 2, 2), ("ant", 31, 4), ("clu", 32, 5), ("uni", 33, 1),
-             ("ant", 1000, 6), ("clu", 5000, 8), ("uni", 70000, 3), ("ant", 70001, 7)]
+             ("ant", 1000, 6), ("clu", 5000, 8), ("uni", 70000, 3), ("ant", 70001, 7),
+             ("uni", 150000, 4)]   # above the single-cluster limit: the multi-kernel path
     for i, (dist, n, d) in enumerate(cases):
         data = make_dataset(dist, n, d, bits=20, seed=100 + i)
         cfg = mk(d)
