@@ -305,6 +305,22 @@ gres_status gres_partition(const uint32_t *d_rows, int64_t n, int32_t d, int32_t
                            const gres_plan_cfg *cfg, void *d_ws, size_t ws_bytes,
                            int64_t *d_part, uint32_t *d_order, uint32_t *d_tile_min, void *stream);
 
+/* gres_compute with the paper's grid parameter (Def. 2, Algorithm 1 with its
+ * g from g_bar down to 2): values are read as fixed point v / 2^bits and the
+ * grid projection at g is floor(v g / 2^bits) -- cells of slightly different
+ * widths when g does not divide 2^bits. Results are indices into h_g: the
+ * first g (in the order given) at which the tuple leaves the skyline, k if
+ * none (the paper's gres = 1); the paper's value is 1 / h_g[index].
+ *   bits   1 .. 32 (values may exceed 2^bits - 1; the projection stays exact)
+ *   h_g    host, k uint32 grid parameters, strictly descending, >= 1
+ * Other arguments as gres_compute; workspace gres_workspace_size(n, d, k). */
+gres_status gres_compute_g(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir, int32_t bits,
+                           const uint32_t *h_g, int32_t k, const gres_plan_cfg *cfg,
+                           void *d_ws, size_t ws_bytes,
+                           int64_t *d_sky_idx, int32_t *d_step_idx,
+                           int64_t *d_sky_count, int64_t *h_sky_count,
+                           unsigned long long *d_tests, void *stream);
+
 /* Grid projection (Sec. 2) of `count` values at each of k widths:
  * d_out[j*count + i] = floor(d_values[i] / h_steps[j]) (the paper's
  * floor(t[i] g) numerator with delta = 2^B / g). Division by a run-time

@@ -316,6 +316,42 @@ gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t d
     return finish_counts(ws, d_sky_count, h_sky_count, st);
 }
 
+gres_status gres_compute_g(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir, int32_t bits,
+                           const uint32_t *h_g, int32_t k, const gres_plan_cfg *cfg,
+                           void *d_ws, size_t ws_bytes,
+                           int64_t *d_sky_idx, int32_t *d_step_idx,
+                           int64_t *d_sky_count, int64_t *h_sky_count,
+                           unsigned long long *d_tests, void *stream) {
+    gres_status s = check_dims(n, d);
+    if (s != GRES_OK) return s;
+    if (dir != GRES_MIN && dir != GRES_MAX) return fail(GRES_EINVAL, "dir must be GRES_MIN or GRES_MAX");
+    if (bits < 1 || bits > 32) return fail(GRES_EINVAL, "bits must be in [1, 32]");
+    if (k < 1 || k > (1 << 20)) return fail(GRES_EINVAL, "k must be in [1, 2^20]");
+    if (!h_g) return fail(GRES_EINVAL, "h_g is NULL");
+    if (h_g[k - 1] < 1) return fail(GRES_EINVAL, "grid parameters must be >= 1");
+    for (int32_t i = 1; i < k; i++)
+        if (h_g[i] >= h_g[i - 1]) return fail(GRES_EINVAL, "grid parameters must be strictly descending");
+    gres_plan_cfg plan;
+    s = check_plan(cfg, d, &plan);
+    if (s != GRES_OK) return s;
+    if (n > 0 && (!d_data || !d_sky_idx || !d_step_idx))
+        return fail(GRES_EINVAL, "d_data / d_sky_idx / d_step_idx is NULL");
+    const size_t need = gres::workspace_layout(n, d, k, nullptr, nullptr);
+    if (!ws_ok(d_ws, ws_bytes, need)) return fail(GRES_EINVAL, "workspace too small, NULL or not 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gres::Workspace ws;
+    gres::workspace_layout(n, d, k, d_ws, &ws);
+    cudaError_t e = gres::launch_init_steps(ws, n, h_g, k, st, bits);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    gres::stage_begin(gres::kStageSkyline, st);
+    e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st);
+    gres::stage_end(gres::kStageSkyline, st);
+    if (e != cudaSuccess) return cuda_fail(e, "skyline");
+    e = gres::launch_gres_stage(d_data, n, d, dir, k, plan, ws, d_sky_idx, d_step_idx, d_tests, st, bits);
+    if (e != cudaSuccess) return cuda_fail(e, "gres stage");
+    return finish_counts(ws, d_sky_count, h_sky_count, st);
+}
+
 gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int32_t dir,
                               const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
                               void *d_ws, size_t ws_bytes,

@@ -59,9 +59,10 @@ __device__ __forceinline__ uint32_t cluster_offset(cg::cluster_group &cl, uint32
                                                    uint32_t *total) {
     if (threadIdx.x == 0) *slot = count;
     cl.sync();
-    const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+    const int r = (int)cl.block_rank();
     uint32_t before = 0, all = 0;
-    for (int q = 0; q < C; q++) {
+    #pragma unroll
+    for (int q = 0; q < kClCTAs; q++) {
         const uint32_t c = *cl.map_shared_rank(slot, q);
         before += q < r ? c : 0u;
         all += c;
@@ -77,10 +78,10 @@ template <int D>
 __device__ __forceinline__ void cluster_range(cg::cluster_group &cl, uint32_t *lo_s, uint32_t *hi_s,
                                               uint32_t (&lo)[D], uint32_t (&hi)[D]) {
     cl.sync();
-    const int C = (int)cl.num_blocks();
     #pragma unroll
     for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
-    for (int c = 0; c < C; c++) {
+    #pragma unroll
+    for (int c = 0; c < kClCTAs; c++) {
         const uint32_t *rl = cl.map_shared_rank(lo_s, c);
         const uint32_t *rh = cl.map_shared_rank(hi_s, c);
         #pragma unroll
@@ -112,9 +113,9 @@ __device__ __forceinline__ void cta_range_add(const uint32_t (&lo)[D], const uin
 __device__ __forceinline__ void cluster_key_range(cg::cluster_group &cl, unsigned long long *kr,
                                                   unsigned long long *kmin, unsigned long long *kmax) {
     cl.sync();
-    const int C = (int)cl.num_blocks();
     unsigned long long a = ~0ull, b = 0ull;
-    for (int c = 0; c < C; c++) {
+    #pragma unroll
+    for (int c = 0; c < kClCTAs; c++) {
         const unsigned long long *x = cl.map_shared_rank(kr, c);
         a = x[0] < a ? x[0] : a;
         b = x[1] > b ? x[1] : b;
@@ -184,7 +185,8 @@ __device__ __forceinline__ void cluster_radix_sort(cg::cluster_group &cl, uint32
         cl.sync();
         if (tid < 256) {
             uint32_t tot = 0, pre = 0;
-            for (int q = 0; q < C; q++) {
+            #pragma unroll
+            for (int q = 0; q < kClCTAs; q++) {   // independent remote loads, all in flight
                 const uint32_t c = cl.map_shared_rank(hist, q)[tid];
                 tot += c;
                 pre += q < r ? c : 0u;
@@ -240,7 +242,8 @@ __device__ __forceinline__ void cluster_radix_sort(cg::cluster_group &cl, uint32
     }
 }
 
-// Launches a cluster kernel: one cluster of kClCTAs CTAs, kClThreads threads,
+// Launches a cluster kernel: one cluster of kClCTAs CTAs (the helpers above
+// assume exactly that many), kClThreads threads,
 // `smem` bytes of dynamic shared memory (the kernel's limit is raised on first
 // use).
 template <typename... KArgs, typename... Args>

@@ -206,6 +206,10 @@ struct DomQuery {
     // position) and the result of position j goes to out[j - t0].
     const uint32_t *iperm = nullptr;
     unsigned t0 = 0, tn = 0;
+    // Grid parameter mode (the paper's g): 0 = integer widths; B = steps are
+    // intervals g over values read as v / 2^B, projection floor(v g / 2^B)
+    // (magic holds g's division constants, steps the pruning widths).
+    int gbits = 0;
 };
 
 // Division constants to make on the device for one query (k_make_magic).
@@ -218,7 +222,8 @@ struct MagicJob {
 // ---- kernel launchers (each queues on `st`, returns the launch error) -------
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
 // Uploads the widths and their division constants and resets the header.
-cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st);
+cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st,
+                              int gbits = 0);
 // Sorts of at most kClusterSortMax items run as one launch of one thread-block
 // cluster; larger ones as three kernels per digit pass.
 constexpr int64_t kClusterSortMax = 131072;
@@ -229,7 +234,7 @@ cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, in
 cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir, int k,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t *d_sky_idx, int32_t *d_step_idx,
-                              unsigned long long *d_tests, cudaStream_t st);
+                              unsigned long long *d_tests, cudaStream_t st, int gbits = 0);
 // The candidate partitioning of the skyline in ws (cand, tmin, perm).
 cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st);
 // The caller's rows as the candidate set (canonical padded rows into

@@ -58,13 +58,21 @@ struct StepChunk {
     uint4 e[kStepChunk];   // (m, s1, s2, delta)
 };
 
+// Steps into device memory: division constants (m, s1, s2, divisor) and the
+// widths the pruning compares excesses with. Widths mode: the width itself.
+// Grid-parameter mode (gbits = B): the divisor is g and the width is
+// floor((2^B - 1) / g) + 1, the widest cell of floor(v g / 2^B) (clamped to
+// 2^32 - 1; that only happens at g = 1, B = 32, where every value falls in
+// one cell and nothing dominates).
 __global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n,
-                               unsigned *zero) {
+                               unsigned *zero, int gbits) {
     if (h) init_header(h, n);
     if (zero && threadIdx.x == 0) *zero = 0u;
     for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
         const uint4 v = c.e[i];
-        steps[c.off + i] = v.w;
+        unsigned long long w = v.w;
+        if (gbits) w = ((1ull << gbits) - 1ull) / v.w + 1ull;
+        steps[c.off + i] = w > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)w;
         reinterpret_cast<uint4 *>(magic)[c.off + i] = v;
     }
 }
@@ -478,19 +486,45 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 }
 
 // Threads per block of the grid-dominance kernels (one block per SM): as many
-// warps as the per-thread registers of each (D, SLOTS) leave room for.
-template <int D, int SLOTS>
+// warps as the per-thread registers of each (D, SLOTS) leave room for. Each
+// of the SM's four sub-partitions holds 16,384 registers and a quarter of the
+// warps, so w warps per sub-partition allow 512 / w registers per thread
+// (rounded down to a multiple of 8): 3 -> 168, 4 -> 128, 5 -> 96, 6 -> 80, 7 -> 72.
+// packed_bounds: the kernels (single query / batch) and (D, SLOTS) for which
+// the packed cell bounds raise the warp count or avoid register spills; the
+// others keep both corners (a few instructions less per test).
+template <int D, int SLOTS, bool BATCH>
+__host__ __device__ constexpr bool packed_bounds() {
+    return BATCH ? !(D == 1 || (SLOTS == 4 && D == 6))
+                 : !(D == 1 || D == 6 || (SLOTS == 8 && D == 4));
+}
+
+template <int D, int SLOTS, bool GM = false>
 __host__ __device__ constexpr int dom_threads() {
-    return SLOTS == 8 ? (D <= 2 ? 640 : D <= 4 ? 512 : D <= 6 ? 384 : 256)
-                      : (D <= 2 ? 768 : D <= 3 ? 640 : D <= 4 ? 576 : D <= 6 ? 512 : 384);
+    return GM ? (SLOTS == 8 ? (D <= 2 ? 640 : D <= 4 ? 512 : D <= 6 ? 384 : 256)
+                            : (D <= 1 ? 896 : D <= 2 ? 768 : D <= 4 ? 640 : D <= 6 ? 512 : 384))
+              : (SLOTS == 8 ? (D <= 1 ? 768 : D <= 3 ? 640 : D <= 5 ? 512 : 384)
+                            : (D <= 2 ? 896 : D <= 3 ? 768 : D <= 5 ? 640 : 512));
 }
 
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
+// Canonical cell [lo, hi] of a target at one width from its stored corner x:
+// the raw cell is [lv, lv + e] with e = min(delta - 1, 2^32 - 1 - lv) (the
+// top cell is cut at 2^32 - 1); canonically that is [lv, lv + e] for
+// smaller-is-better (x = lv, 2^32 - 1 - lv = ~x) and [~lv - e, ~lv] for
+// larger-is-better (x = ~lv, 2^32 - 1 - lv = x). A zero corner with dir 0 or 1
+// gives lo = 0, so nothing is strictly below it (lanes past K).
+__device__ __forceinline__ void cell_bounds(uint32_t x, uint32_t dm1, int dir, uint32_t &lo, uint32_t &hi) {
+    const uint32_t e = min(dm1, dir ? x : ~x);
+    lo = dir ? x - e : x;
+    hi = dir ? x : x + e;
+}
+
 // Grid resistance of the target at partition position i of query q (one
 // warp; every lane returns it): the first step at which some candidate's
 // projection dominates the target's projection, else K.
-template <int D, int SLOTS, bool RES>
+template <int D, int SLOTS, bool RES, bool PK, bool GM>
 __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
                                            const uint32_t *smin, long long T, unsigned i, uint32_t *wsteps,
                                            unsigned long long &n_tests, unsigned long long &n_checks) {
@@ -509,8 +543,13 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
             wsteps[32 * j + lane] = k < K ? __ldg(qy.steps + k) : 0xFFFFFFFFu;
         }
         __syncwarp();
-        uint32_t U[SLOTS][D], L[SLOTS][D];
-        unsigned ready = 0;   // slots whose bounds are in U, L
+        // Cell of the target at the slot's width, in canonical values. Unpacked: both
+        // corners per attribute (X high, Y low). Packed (fewer registers, so more
+        // warps per SM where that matters): one corner per attribute, X = the low
+        // corner (smaller-is-better) or the high corner (larger-is-better), plus
+        // the width minus one per slot; see cell_bounds.
+        uint32_t X[SLOTS][D], Y[PK ? 1 : SLOTS][PK ? 1 : D], dm1[PK ? SLOTS : 1];
+        unsigned ready = 0;   // slots whose bounds are made
         int best = wcount;
         // keys hold excesses >> qshift; only excesses below the window's widest width matter
         const uint32_t wmax = wsteps[wcount - 1];
@@ -618,21 +657,48 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                                 const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
                                                       : make_uint4(1u, 0u, 0u, 1u);
                                 const uint32_t delta = mg.w;
+                                if (PK) dm1[PK ? j : 0] = delta - 1u;
                                 #pragma unroll
                                 for (int q = 0; q < D; q++) {
                                     const uint32_t v = qy.dir ? ~t[q] : t[q];
+                                    if (GM) {
+                                        // cell of floor(v g / 2^B): with v g = c 2^B + r it is
+                                        // [v - floor(r / g), v + floor((2^B - 1 - r) / g)]
+                                        const unsigned long long mask = (1ull << qy.gbits) - 1ull;
+                                        const uint32_t r = (uint32_t)(((unsigned long long)v * delta) & mask);
+                                        const uint32_t lv = v - udiv(r, mg.x, mg.y, mg.z);
+                                        const unsigned long long u =
+                                            (unsigned long long)v + udiv((uint32_t)(mask - r), mg.x, mg.y, mg.z);
+                                        const uint32_t uv = u > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)u;
+                                        X[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
+                                        Y[PK ? 0 : j][PK ? 0 : q] = live ? (qy.dir ? ~uv : lv) : 0u;
+                                        continue;
+                                    }
                                     const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
-                                    const uint32_t uv =
-                                        lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
-                                    U[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
-                                    L[j][q] = live ? (qy.dir ? ~uv : lv) : 0u;
+                                    if (PK) {
+                                        // raw cell [lv, lv + min(delta - 1, ~lv)]: canonical low corner lv
+                                        // (MIN) or canonical high corner ~lv (MAX); lanes past K never match
+                                        X[j][q] = live ? (qy.dir ? ~lv : lv) : 0u;
+                                    } else {
+                                        const uint32_t uv =
+                                            lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+                                        X[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
+                                        Y[PK ? 0 : j][PK ? 0 : q] = live ? (qy.dir ? ~uv : lv) : 0u;
+                                    }
                                 }
                             }
                             bool le = true, lt = false;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                le &= sc[q] <= U[j][q];
-                                lt |= sc[q] < L[j][q];
+                                uint32_t lo, hi;
+                                if (PK) {
+                                    cell_bounds(X[j][q], dm1[PK ? j : 0], qy.dir, lo, hi);
+                                } else {
+                                    hi = X[j][q];
+                                    lo = Y[PK ? 0 : j][PK ? 0 : q];
+                                }
+                                le &= sc[q] <= hi;
+                                lt |= sc[q] < lo;
                             }
                             n_tests += 32;
                             const unsigned msk = __ballot_sync(kFull, le & lt);
@@ -654,8 +720,8 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
     return result;
 }
 
-template <int D, int SLOTS>
-__global__ void __launch_bounds__(dom_threads<D, SLOTS>(), 1)
+template <int D, int SLOTS, bool GM>
+__global__ void __launch_bounds__(dom_threads<D, SLOTS, GM>(), 1)
 k_dominance(DomArgs a) {
     constexpr int DP = padded_dims(D);
     constexpr int WS = 32 * SLOTS;
@@ -688,7 +754,8 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            const int r = dom_target<D, SLOTS, true>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T,
+            constexpr bool PK = !GM && packed_bounds<D, SLOTS, false>();
+            const int r = dom_target<D, SLOTS, true, PK, GM>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T,
                                                      i, wsteps, n_tests, n_checks);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
@@ -698,7 +765,8 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            const int r = dom_target<D, SLOTS, false>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests,
+            constexpr bool PK = !GM && packed_bounds<D, SLOTS, false>();
+            const int r = dom_target<D, SLOTS, false, PK, GM>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests,
                                                       n_checks);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
@@ -754,7 +822,9 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
         const long long T = (S + kTileRows - 1) / kTileRows;
         const unsigned local = (unsigned)(g - first[lo]);
         const unsigned i = q.iperm ? __ldg(q.iperm + q.t0 + local) : local;
-        const int r = dom_target<D, SLOTS, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests, n_checks);
+        constexpr bool PK = packed_bounds<D, SLOTS, true>();
+        const int r = dom_target<D, SLOTS, false, PK, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
+                                                             n_checks);
         if (lane == 0) q.out[q.iperm ? local : q.perm[i]] = r;
     }
 }
@@ -812,18 +882,18 @@ cudaError_t device_props() {
     return cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 }
 
-template <int D, int SLOTS>
+template <int D, int SLOTS, bool GM>
 cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
     static bool configured = false;
     const int smem = g_smem_optin;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_dominance<D, SLOTS>,
+        cudaError_t e = cudaFuncSetAttribute(k_dominance<D, SLOTS, GM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     a.smem_words = smem / 4;
-    k_dominance<D, SLOTS><<<g_sm_count, dom_threads<D, SLOTS>(), smem, st>>>(a); note_launch();
+    k_dominance<D, SLOTS, GM><<<g_sm_count, dom_threads<D, SLOTS, GM>(), smem, st>>>(a); note_launch();
     return cudaGetLastError();
 }
 
@@ -891,7 +961,8 @@ cudaError_t dominance_d(int slots, const DomQuery &q, unsigned *counter, unsigne
     a.counter = counter;
     a.tests = tests;
     a.smem_words = 0;
-    return slots == 4 ? launch_dom<D, 4>(a, st) : launch_dom<D, 8>(a, st);
+    if (q.gbits) return slots == 4 ? launch_dom<D, 4, true>(a, st) : launch_dom<D, 8, true>(a, st);
+    return slots == 4 ? launch_dom<D, 4, false>(a, st) : launch_dom<D, 8, false>(a, st);
 }
 
 template <int D>
@@ -929,12 +1000,13 @@ cudaError_t launch_upload_steps(uint32_t *d_steps, uint32_t *d_magic, unsigned *
             udiv_magic(h_steps[off + i], &m, &s1, &s2);
             c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
         }
-        k_upload_steps<<<1, 256, 0, st>>>(c, d_steps, d_magic, nullptr, 0, off == 0 ? zero : nullptr); note_launch();
+        k_upload_steps<<<1, 256, 0, st>>>(c, d_steps, d_magic, nullptr, 0, off == 0 ? zero : nullptr, 0); note_launch();
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st) {
+cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st,
+                              int gbits) {
     StepChunk c;
     for (int off = 0; off < k; off += kStepChunk) {
         c.off = off;
@@ -945,7 +1017,7 @@ cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps,
             c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
         }
         k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic, off == 0 ? ws.hdr : nullptr, (long long)n,
-                                          nullptr); note_launch();
+                                          nullptr, gbits); note_launch();
     }
     return cudaGetLastError();
 }
@@ -1024,7 +1096,7 @@ cudaError_t launch_make_magic(const MagicJob *jobs, int count, cudaStream_t st) 
 cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int dir, int k,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t * /*d_sky_idx*/, int32_t *d_step_idx,
-                              unsigned long long *d_tests, cudaStream_t st) {
+                              unsigned long long *d_tests, cudaStream_t st, int gbits) {
     if (n == 0) return cudaSuccess;
     stage_begin(kStagePartition, st);
     cudaError_t e = launch_partition(d, cfg, n, ws, st);
@@ -1041,6 +1113,7 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
     q.out = d_step_idx;
     q.K = k;
     q.dir = dir;
+    q.gbits = gbits;
     stage_begin(kStageDominance, st);
     e = launch_dominance(d, cfg.slots, q, &ws.hdr->work_next,
                          (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr, st);

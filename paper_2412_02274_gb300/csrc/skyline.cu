@@ -260,17 +260,23 @@ __global__ void k_sel_gather(const unsigned long long *keys, long long n, WsHead
     }
 }
 
-// Orders the candidates spatially -- by the Morton code of their rows over the
-// candidates' bounding box, then by row -- with a bitonic sort in one block,
-// and writes their canonical rows to `rows` in that order. Spatially tight
-// runs of 32 representatives let the filter skip whole runs.
+// Orders the representatives spatially -- by the Morton code of their rows
+// over their bounding box, then by row -- with a bitonic sort in one block
+// (compare-exchange steps with partners less than 32 apart through warp
+// shuffles, the others through shared memory), and writes their canonical
+// rows to `rows` in that order. Spatially tight runs of 32 representatives
+// let the filter skip whole runs. Representatives dominated by another
+// representative stay: by transitivity the filter drops exactly the same
+// rows with or without them. Also clears the filter's per-segment survivor
+// counts (nb of them).
 template <int D>
 __global__ void __launch_bounds__(kMaxReps)
 k_rep_sort(const uint32_t *data, int dir, const unsigned long long *rep_key, const uint32_t *rep_idx,
-           WsHeader *h, uint32_t *rows) {
+           WsHeader *h, uint32_t *rows, uint32_t *blocksum, long long nb) {
     __shared__ unsigned long long sk[kMaxReps];
     __shared__ uint32_t lo[D], hi[D];
     const int tid = threadIdx.x;
+    for (long long j = tid; j < nb; j += kMaxReps) blocksum[j] = 0u;
     const int nc = (int)min((long long)h->n_cand, (long long)kMaxReps);
     if (tid < D) { lo[tid] = 0xFFFFFFFFu; hi[tid] = 0u; }
     __syncthreads();
@@ -283,91 +289,32 @@ k_rep_sort(const uint32_t *data, int dir, const unsigned long long *rep_key, con
     }
     __syncthreads();
     const int bits = min(16, 32 / D);
-    sk[tid] = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 32) | idx : ~0ull;
-    __syncthreads();
+    unsigned long long v = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 32) | idx : ~0ull;
     for (int size = 2; size <= kMaxReps; size <<= 1) {
+        const bool asc = (tid & size) == 0;
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const int j = tid ^ stride;
-            if (j > tid) {
-                const bool asc = (tid & size) == 0;
-                if ((sk[tid] > sk[j]) == asc) {
-                    unsigned long long tk = sk[tid]; sk[tid] = sk[j]; sk[j] = tk;
-                }
+            unsigned long long other;
+            if (stride >= 32) {
+                sk[tid] = v;
+                __syncthreads();
+                other = sk[tid ^ stride];
+                __syncthreads();
+            } else {
+                other = __shfl_xor_sync(0xffffffffu, v, stride);
             }
-            __syncthreads();
+            const bool lower = (tid & stride) == 0;
+            const unsigned long long mn = other < v ? other : v, mx = other < v ? v : other;
+            v = (asc == lower) ? mn : mx;
         }
     }
     if (tid < nc) {
-        load_canon<D>(data, (uint32_t)(sk[tid] & 0xFFFFFFFFull), dir, x);
+        load_canon<D>(data, (uint32_t)(v & 0xFFFFFFFFull), dir, x);
         store_row<D>(rows, tid, x);
     }
-    if (tid == 0) h->n_cand = nc;
-}
-
-// Keeps the non-dominated candidates, in order, in place (run by the last
-// block of k_rep_flags, 1024 threads).
-template <int D>
-__device__ __forceinline__ void rep_compact(uint32_t *rows, const uint32_t *rep_flag, WsHeader *h) {
-    __shared__ uint32_t wsum[kMaxReps / 32];
-    __syncthreads();
-    const int i = threadIdx.x;
-    const int nc = (int)h->n_cand;
-    const bool keep = i < nc && rep_flag[i] != 0u;
-    uint32_t x[D];
-    if (keep) load_row<D>(rows, i, x);
-    const int lane = i & 31, w = i >> 5;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) wsum[w] = __popc(bal);
-    __syncthreads();
-    uint32_t before = 0, all = 0;
-    for (int j = 0; j < kMaxReps / 32; j++) {
-        before += j < w ? wsum[j] : 0u;
-        all += wsum[j];
+    if (tid == 0) {
+        h->n_cand = nc;
+        h->n_reps = nc;
     }
-    if (keep) store_row<D>(rows, before + __popc(bal & ((1u << lane) - 1u)), x);
-    if (i == 0) h->n_reps = all;
-}
-
-// Representatives dominated by another one are dropped (Sec. 3.1). One warp
-// per candidate, lanes over the other candidates (all staged in shared
-// memory by every block).
-constexpr int kRepBlock = 1024;
-template <int D>
-__global__ void __launch_bounds__(kRepBlock)
-k_rep_flags(uint32_t *cand_rows, WsHeader *h, uint32_t *rep_flag, uint32_t *blocksum, long long nb) {
-    __shared__ uint32_t rows[D * kMaxReps];
-    const int nc = (int)h->n_cand;
-    // the filter's per-segment survivor counts start at zero
-    for (long long j = (long long)blockIdx.x * kRepBlock + threadIdx.x; j < nb; j += (long long)gridDim.x * kRepBlock)
-        blocksum[j] = 0u;
-    for (int i = threadIdx.x; i < nc; i += kRepBlock) {
-        uint32_t x[D];
-        load_row<D>(cand_rows, i, x);
-        #pragma unroll
-        for (int q = 0; q < D; q++) rows[q * kMaxReps + i] = x[q];
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (kRepBlock / 32) + (threadIdx.x >> 5);
-    if (i < nc) {
-        uint32_t x[D];
-        #pragma unroll
-        for (int q = 0; q < D; q++) x[q] = rows[q * kMaxReps + i];
-        bool dom = false;
-        for (int j0 = 0; j0 < nc && !dom; j0 += 32) {
-            const int j = j0 + lane;
-            bool hit = false;
-            if (j < nc) {
-                uint32_t sv[D];
-                #pragma unroll
-                for (int q = 0; q < D; q++) sv[q] = rows[q * kMaxReps + j];
-                hit = dominates<D>(sv, x);
-            }
-            dom = __any_sync(0xffffffffu, hit);
-        }
-        if (lane == 0) rep_flag[i] = dom ? 0u : 1u;
-    }
-    if (last_block_done(&h->done[1])) rep_compact<D>(cand_rows, rep_flag, h);
 }
 
 // Survivor flags (not dominated by any representative), rows in input order,
@@ -814,9 +761,8 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 1, ws.sel_hist, reps); note_launch();
     k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 2, ws.sel_hist + kSelBuckets, reps); note_launch();
     k_sel_gather<<<gb, 256, 0, st>>>(ws.keys[0], n, ws.hdr, ws.rep_key, ws.rep_idx); note_launch();
-    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps); note_launch();
-    const int r_eff = (int)std::min<int64_t>(reps, n);
-    k_rep_flags<D><<<(r_eff + 31) / 32, kRepBlock, 0, st>>>(ws.reps, ws.hdr, ws.perm, ws.blocksum, nb); note_launch();
+    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps, ws.blocksum,
+                                          nb); note_launch();
     static int filter_blocks = 0;   // resident blocks of k_filter<D> on this GPU
     if (filter_blocks == 0) {
         int per_sm = 0, dev = 0, sms = 0;

@@ -86,6 +86,8 @@ def load():
         lib.gres_compute_host.argtypes = [_p, _i64, _i32, _i32, _p, _i32, ctypes.POINTER(PlanCfg),
                                           _p, _size, _p, _p, _p, _p]
         lib.gres_gproj.argtypes = [_p, _i64, _p, _i32, _p, _p]
+        lib.gres_compute_g.argtypes = [_p, _i64, _i32, _i32, _i32, _p, _i32, ctypes.POINTER(PlanCfg),
+                                       _p, _size, _p, _p, _p, _p, _p, _p]
         lib.gres_partition.argtypes = [_p, _i64, _i32, _i32, ctypes.POINTER(PlanCfg), _p, _size,
                                        _p, _p, _p, _p]
         lib.gres_udiv_magic.argtypes = [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
@@ -262,6 +264,28 @@ def gres_compute(data, steps, direction: int = MIN, cfg: PlanCfg | None = None,
     if sync:
         return sky[: cnt.value], res[: cnt.value]
     return sky, res, dcnt
+
+
+def gres_compute_g(data, bits: int, g_list, direction: int = MIN, cfg: PlanCfg | None = None,
+                   ws: Workspace | None = None, stream=None, tests=None):
+    """The paper's grid-parameter form: projection floor(v g / 2^bits) for each g of
+    ``g_list`` (strictly descending). Returns ``(sky_idx[S], idx[S])`` CUDA tensors, idx
+    the first position in ``g_list`` at which the tuple leaves the skyline, len(g_list)
+    if never (the paper's gres = 1)."""
+    torch = _torch()
+    n, d = int(data.shape[0]), int(data.shape[1])
+    gl = _steps_array(g_list)
+    k = len(gl)
+    ws = ws or alloc_workspace(n, d, k)
+    sky = torch.empty(max(n, 1), dtype=torch.int64, device=data.device)
+    res = torch.empty(max(n, 1), dtype=torch.int32, device=data.device)
+    cfgp = ctypes.byref(cfg) if cfg is not None else None
+    cnt = ctypes.c_int64(0)
+    _check(load().gres_compute_g(_ptr(data), n, d, int(direction), int(bits),
+                                 gl.ctypes.data_as(ctypes.c_void_p), k, cfgp,
+                                 _ptr(ws.tensor), ws.nbytes, _ptr(sky), _ptr(res), None,
+                                 ctypes.byref(cnt), _ptr(tests), _stream_ptr(stream)))
+    return sky[: cnt.value], res[: cnt.value]
 
 
 def gres_compute_host(data_host, steps, direction: int = MIN, cfg: PlanCfg | None = None,

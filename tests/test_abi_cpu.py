@@ -133,3 +133,14 @@ def test_partition_argument_checks_need_no_gpu():
     assert rc == 1 and b"workspace" in lib.gres_last_error()
     rc = lib.gres_partition(fake, 10, 2, 0, None, ctypes.c_void_p(260), 1 << 30, fake, fake, fake, None)
     assert rc == 1
+
+
+def test_gmode_argument_checks_need_no_gpu():
+    lib = G.load()
+    fake = ctypes.c_void_p(256)
+    cnt = ctypes.c_int64(0)
+    for bits, gl in [(0, [4, 2]), (33, [4, 2]), (20, [2, 4]), (20, [3, 3]), (20, [2, 0])]:
+        g = np.array(gl, np.uint32)
+        rc = lib.gres_compute_g(fake, 10, 2, 0, bits, g.ctypes.data_as(ctypes.c_void_p), len(g), None,
+                                fake, 1 << 30, fake, fake, None, ctypes.byref(cnt), None, None)
+        assert rc == 1, (bits, gl)
