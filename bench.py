@@ -48,7 +48,7 @@ WORKLOADS = {
     "uni-n1000-d2-b16-k64-grid": ("uni", 1_000, 2, 16, ("lin", 64, 64), "grid", 0, 0),
 }
 DEFAULT_WORKLOAD = "ant-n100000-d4-b20-k256-grid-m4"
-MULTI_WORKLOADS = ("batch-512", "serve-10k")
+MULTI_WORKLOADS = ("batch-512", "serve-10k", "sweep")
 SCHEMES = {"none": 0, "grid": 1, "angular": 2, "sliced": 3}
 METRIC = "effective grid-dominance tests/s (skyline + gres of every skyline tuple)"
 UNIT = "tests/s"
@@ -525,6 +525,94 @@ def run_batch(args):
     return 0
 
 
+# ---- the paper's operating-parameter sweep (Table 1) ---------------------------------
+def table1_plan(scheme: str, d: int, p_target: int):
+    """(m or p) closest to the target partition count, with more than one partition (as the
+    paper does for Grid m^d and Angular m^(d-1))."""
+    if scheme in ("grid", "angular"):
+        dims = d if scheme == "grid" else d - 1
+        if dims < 1:
+            return 1, 1
+        best = None
+        for m in range(2, 65):
+            cells = m ** dims
+            if cells >= 1 << 32:
+                break
+            score = abs(np.log(cells) - np.log(p_target))
+            if best is None or score < best[0]:
+                best = (score, m, cells)
+        return best[1], best[2]
+    if scheme == "sliced":
+        return p_target, p_target
+    return 0, 1
+
+
+def run_sweep(args):
+    """Dominance tests and time per partitioning scheme over the paper's operating
+    parameters (Table 1): N, d, partitions, representatives; UNI and ANT; the practical
+    g_bar = 25 (g = 25 .. 2) on 20-bit values. Counters: lane-tests of the grid-dominance
+    kernel and pruning checks (GRES_FLAG_COUNT_TESTS)."""
+    import torch
+    from paper_2412_02274_gb300 import gres as G
+    dev = torch.device("cuda", torch.cuda.current_device())
+    glist = np.arange(25, 1, -1, dtype=np.uint32)
+    configs = []
+    for dist in ("uni", "ant"):
+        for n in (100_000, 500_000, 1_000_000, 5_000_000, 10_000_000):
+            configs.append((dist, n, 3, 16, 0))
+        for d in (2, 4, 5, 6, 7):
+            configs.append((dist, 1_000_000, d, 16, 0))
+        for p in (32, 64, 128):
+            configs.append((dist, 1_000_000, 3, p, 0))
+        for reps in (1, 10, 100, 1000):
+            configs.append((dist, 1_000_000, 3, 16, reps))
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+    for dist, n, d, p_target, reps in configs:
+        data = make_dataset(dist, n, d, bits=20, seed=0)
+        x = G.to_device_u32(data, dev)
+        ws = G.alloc_workspace(n, d, len(glist))
+        for scheme in ("grid", "angular", "sliced", "none"):
+            mp, cells = table1_plan(scheme, d, p_target)
+            kw = {"m": mp} if scheme in ("grid", "angular") else ({"p": mp} if scheme == "sliced" else {})
+            cfg = G.plan(SCHEMES[scheme], reps=reps, **kw)
+            G.gres_compute_g(x, 20, glist, G.MIN, cfg, ws=ws, stream=stream)    # warm-up
+            tests = torch.zeros(2, dtype=torch.int64, device=dev)
+            cfg_c = G.plan(SCHEMES[scheme], reps=reps, count_tests=True, **kw)
+            sky, idx = G.gres_compute_g(x, 20, glist, G.MIN, cfg_c, ws=ws, stream=stream, tests=tests)
+            lane_tests, checks = (int(v) for v in tests.cpu().tolist())
+            G.timing_enable(True)
+            G.timing_read()
+            t = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                G.gres_compute_g(x, 20, glist, G.MIN, cfg, ws=ws, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                t.append(a.elapsed_time(b))
+            st = G.timing_read()
+            G.timing_enable(False)
+            S = int(sky.numel())
+            rows.append({"dist": dist, "n": n, "d": d, "p_target": p_target, "reps": reps or 1024,
+                         "scheme": scheme, "param": mp, "partitions": cells, "S": S,
+                         "lane_tests": lane_tests, "pruning_checks": checks,
+                         "dense_tests": S * S * len(glist),
+                         "ms": float(np.median(t)), "skyline_ms": st["skyline"][0] / max(st["skyline"][1], 1),
+                         "partition_ms": st["partition"][0] / max(st["partition"][1], 1),
+                         "dominance_ms": st["dominance"][0] / max(st["dominance"][1], 1)})
+            print(json.dumps({"row": rows[-1]}), file=sys.stderr, flush=True)
+        del x, ws
+        torch.cuda.empty_cache()
+    line = {"metric": "dominance tests and time per scheme (Table 1 sweep)", "value": len(rows),
+            "unit": "configurations", "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": "sweep", "g": "25..2", "value_bits": 20,
+                                            "seed": 0}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---- serving ----------------------------------------------------------------------
 def serve_datasets(count=64, seed=1):
     """64 datasets: N log-uniform in [1e3, 2e6], d in {2..8}, UNI / ANT / CLU mix."""
@@ -635,6 +723,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "serve-10k":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -554,6 +554,10 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
         // keys hold excesses >> qshift; only excesses below the window's widest width matter
         const uint32_t wmax = wsteps[wcount - 1];
         const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
+        // wl: the width of step best - 1 (excesses at or above it cannot matter), wlq: its key
+        uint32_t wl = wmax, wlq = min(wmax >> qshift, 0x7FFFFFFu);
+        // lane j < SLOTS - 1 holds the widest width of slot j (for the first slot that can matter)
+        const uint32_t slot_top = (lane < SLOTS - 1 && 32 * lane + 31 < wcount) ? wsteps[32 * lane + 31] : 0xFFFFFFFFu;
         // Best-first over three levels -- 1024-row super-tiles, 32-row tiles, rows --
         // each visited in ascending order of its lower bound on the excess
         // max_i (s_i - t_i)^+ (keys hold it >> qshift, 27 bits; exact tests below).
@@ -571,7 +575,7 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                     emax = max(emax, mn[q] > t[q] ? mn[q] - t[q] : 0u);
                     can |= mn[q] < t[q];
                 }
-                if (can && emax < wsteps[best - 1]) {
+                if (can && emax < wl) {
                     sex = emax;
                     skey = (min(emax >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane;
                 }
@@ -580,8 +584,7 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
             for (;;) {
                 const uint32_t mk = __reduce_min_sync(kFull, skey);
                 if (mk == kNoTile) break;
-                const uint32_t wl = wsteps[best - 1];
-                if ((mk >> 5) > min(wl >> qshift, 0x7FFFFFFu)) break;   // every super-tile left is too far
+                if ((mk >> 5) > wlq) break;   // every super-tile left is too far
                 const int sl = (int)(mk & 31u);
                 if (lane == sl) skey = kNoTile;
                 if (__shfl_sync(kFull, sex, sl) >= wl) continue;
@@ -608,11 +611,10 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                 for (;;) {
                     const uint32_t tk = __reduce_min_sync(kFull, tkey);
                     if (tk == kNoTile) break;
-                    const uint32_t wlim = wsteps[best - 1];
-                    if ((tk >> 5) > min(wlim >> qshift, 0x7FFFFFFu)) break;   // every tile left is too far
+                    if ((tk >> 5) > wlq) break;   // every tile left is too far
                     const int tl = (int)(tk & 31u);
                     if (lane == tl) tkey = kNoTile;
-                    if (__shfl_sync(kFull, tex, tl) >= wlim) continue;
+                    if (__shfl_sync(kFull, tex, tl) >= wl) continue;
                     const long long r0 = (sup * 32 + tl) * kTileRows;
                     // candidate level: lane r looks at row r of the tile
                     uint32_t s[D];
@@ -627,25 +629,23 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                     n_checks += 32;
                     // a row can dominate t only at widths wider than e_r; it matters only if such
                     // a width comes before best. Rows are taken in ascending order of e_r.
-                    uint32_t ckey = (can_r && e_r < wlim) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
-                                                          : 0xFFFFFFFFu;
+                    uint32_t ckey = (can_r && e_r < wl) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
+                                                        : 0xFFFFFFFFu;
                     for (;;) {
                         const uint32_t ck = __reduce_min_sync(kFull, ckey);
                         if (ck == 0xFFFFFFFFu) break;
                         const int c = (int)(ck & 31u);
                         if (lane == c) ckey = 0xFFFFFFFFu;
                         const uint32_t ec = __shfl_sync(kFull, e_r, c);
-                        if (ec >= wsteps[best - 1]) {
-                            if ((ck >> 5) > min(wsteps[best - 1] >> qshift, 0x7FFFFFFu)) break;
+                        if (ec >= wl) {
+                            if ((ck >> 5) > wlq) break;
                             continue;
                         }
                         uint32_t sc[D];
                         #pragma unroll
                         for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
                         // first slot holding a width wider than ec
-                        int jlo = 0;
-                        #pragma unroll
-                        for (int j = 0; j < SLOTS - 1; j++) jlo += (32 * j + 31 < wcount && wsteps[32 * j + 31] <= ec) ? 1 : 0;
+                        const int jlo = __popc(__ballot_sync(kFull, slot_top <= ec));
                         const int jhi = (best - 1) >> 5;
                         #pragma unroll
                         for (int j = 0; j < SLOTS; j++) {
@@ -704,6 +704,10 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                             const unsigned msk = __ballot_sync(kFull, le & lt);
                             if (msk) {
                                 best = min(best, 32 * j + __ffs(msk) - 1);
+                                if (best > 0) {
+                                    wl = wsteps[best - 1];
+                                    wlq = min(wl >> qshift, 0x7FFFFFFu);
+                                }
                                 break;
                             }
                         }
