@@ -414,7 +414,7 @@ gres_status gres_partition(const uint32_t *d_rows, int64_t n, int32_t d, int32_t
     if (e != cudaSuccess) return cuda_fail(e, "load");
     e = gres::launch_partition(d, plan, n, ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "partition");
-    e = gres::launch_partition_out(d, plan.scheme, n, ws, d_part, d_order, d_tile_min, st);
+    e = gres::launch_partition_out(d, plan, n, ws, d_part, d_order, d_tile_min, st);
     if (e != cudaSuccess) return cuda_fail(e, "partition output");
     return GRES_OK;
 }

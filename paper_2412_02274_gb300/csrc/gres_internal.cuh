@@ -243,7 +243,7 @@ cudaError_t launch_load_candidates(const uint32_t *d_rows, int64_t n, int d, int
                                    cudaStream_t st);
 // Partition numbers by row, the tile order and the tile minima (d words per
 // tile) after launch_partition.
-cudaError_t launch_partition_out(int d, int scheme, int64_t n, Workspace &ws, int64_t *d_part,
+cudaError_t launch_partition_out(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, int64_t *d_part,
                                  uint32_t *d_order, uint32_t *d_tile_min, cudaStream_t st);
 // The grid-dominance kernel for one query; *counter must be 0.
 cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,

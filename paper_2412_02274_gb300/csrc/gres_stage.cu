@@ -123,6 +123,8 @@ struct PartArgs {
     int m;           // GRID / ANGULAR slices
     int p;           // SLICED partitions
     int dim;         // SLICED attribute
+    int bpa;         // bits per attribute of the order inside a partition
+    int obits;       // bpa * D: the key is partition << obits | order
     unsigned long long thr[64];   // ANGULAR: tan^2(j pi / 2m) * 2^32, j = 1 .. m-1
 };
 
@@ -151,24 +153,30 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&x)[D], int q) {
     return v;
 }
 
-// Order inside a partition: a 16-bit Morton code of x = v - lo over the
-// skyline's range (16 / D bits per attribute), so that 32 consecutive rows of a
-// partition are spatially tight.
+// Order inside a partition: a Morton code (bpa bits per attribute) so that 32
+// consecutive rows of a partition are spatially tight. The partition number
+// and the code share one sort key of at most 16 bits where the partition
+// count allows (two 8-bit radix passes).
 template <int D>
-__device__ __forceinline__ unsigned long long morton16(const uint32_t (&x)[D], const WsHeader *h) {
-    const int bits = 16 / D;
-    uint32_t q[D];
-    #pragma unroll
-    for (int i = 0; i < D; i++) {
-        const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
-        q[i] = (uint32_t)(((unsigned long long)x[i] << bits) / span);
-    }
+__device__ __forceinline__ unsigned long long interleave(const uint32_t (&q)[D], int bpa) {
     unsigned long long key = 0;
-    for (int b = bits - 1; b >= 0; b--) {
+    for (int b = bpa - 1; b >= 0; b--) {
         #pragma unroll
         for (int i = 0; i < D; i++) key = (key << 1) | ((q[i] >> b) & 1u);
     }
     return key;
+}
+
+// Over the skyline's range: x = v - lo quantized to bpa bits per attribute.
+template <int D>
+__device__ __forceinline__ unsigned long long morton_range(const uint32_t (&x)[D], const WsHeader *h, int bpa) {
+    uint32_t q[D];
+    #pragma unroll
+    for (int i = 0; i < D; i++) {
+        const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
+        q[i] = (uint32_t)(((unsigned long long)x[i] << bpa) / span);
+    }
+    return interleave<D>(q, bpa);
 }
 
 // Partition numbers (Sec. 3.1) on coordinates x = v - lo (canonical):
@@ -177,7 +185,9 @@ __device__ __forceinline__ unsigned long long morton16(const uint32_t (&x)[D], c
 //            thresholds j pi / 2m reached, decided exactly as
 //            (Y << 32) >= X * thr_j in 128-bit integers (Eq. 1)
 //   SLICED:  first pass keys on x_dim; the slice comes from the rank.
-// Sort key = partition << 16 | morton16 (order inside a partition), value = row.
+// Sort key = partition << obits | order inside the partition, value = row.
+// GRID orders a cell by the Morton code of the position inside the cell,
+// x_i m - c_i span_i in [0, span_i); the others by the code over the range.
 template <int D>
 __device__ __forceinline__ unsigned long long part_key(const uint32_t *sky_rows, long long j, const WsHeader *h,
                                                        const PartArgs &a) {
@@ -188,13 +198,17 @@ __device__ __forceinline__ unsigned long long part_key(const uint32_t *sky_rows,
     unsigned long long pid = 0;
     if (a.scheme == GRES_PART_GRID) {
         unsigned long long w = 1;
+        uint32_t q[D];
         #pragma unroll
         for (int i = 0; i < D; i++) {
             const unsigned long long span = (unsigned long long)(h->hi[i] - h->lo[i]) + 1ull;
-            pid += ((unsigned long long)x[i] * (unsigned long long)a.m) / span * w;
+            const unsigned long long xm = (unsigned long long)x[i] * (unsigned long long)a.m;
+            const unsigned long long c = xm / span;
+            pid += c * w;
             w *= (unsigned long long)a.m;
+            q[i] = (uint32_t)(((xm - c * span) << a.bpa) / span);
         }
-        return (pid << 16) | morton16<D>(x, h);
+        return (pid << a.obits) | interleave<D>(q, a.bpa);
     }
     if (a.scheme == GRES_PART_ANGULAR) {
         unsigned long long w = 1;
@@ -212,13 +226,13 @@ __device__ __forceinline__ unsigned long long part_key(const uint32_t *sky_rows,
             pid += (unsigned long long)bin * w;
             w *= (unsigned long long)a.m;
         }
-        return (pid << 16) | morton16<D>(x, h);
+        return (pid << a.obits) | morton_range<D>(x, h, a.bpa);
     }
     return pick<D>(x, a.dim);   // SLICED, first pass
 }
 
 // SLICED second pass key of the row of rank r (its row j read from the
-// sorted values): slice floor(r p / S) << 16 | morton16.
+// sorted values): slice floor(r p / S) << obits | Morton code over the range.
 template <int D>
 __device__ __forceinline__ unsigned long long sliced_key(const uint32_t *sky_rows, uint32_t j, long long r,
                                                          long long S, const WsHeader *h, const PartArgs &a) {
@@ -227,7 +241,7 @@ __device__ __forceinline__ unsigned long long sliced_key(const uint32_t *sky_row
     const unsigned long long slice = (unsigned long long)r * (unsigned long long)a.p / (unsigned long long)S;
     #pragma unroll
     for (int q = 0; q < D; q++) x[q] -= h->lo[q];
-    return (slice << 16) | morton16<D>(x, h);
+    return (slice << a.obits) | morton_range<D>(x, h, a.bpa);
 }
 
 template <int D>
@@ -455,7 +469,7 @@ __global__ void k_load_candidates(const uint32_t *rows, int dir, long long n, ui
 template <int D>
 __global__ void k_partition_out(const WsHeader *h, const unsigned long long *keys0,
                                 const unsigned long long *keys1, const uint32_t *perm,
-                                const uint32_t *tmin, int scheme, long long n, int64_t *part,
+                                const uint32_t *tmin, int scheme, int obits, long long n, int64_t *part,
                                 uint32_t *order, uint32_t *tile_min) {
     constexpr int DP = padded_dims(D);
     const unsigned long long *keys = h->sorted_sel ? keys1 : keys0;
@@ -466,7 +480,7 @@ __global__ void k_partition_out(const WsHeader *h, const unsigned long long *key
         if (r < n) {
             const uint32_t j = perm[r];
             order[r] = j;
-            part[j] = scheme == GRES_PART_NONE ? 0 : (int64_t)(keys[r] >> 16);
+            part[j] = scheme == GRES_PART_NONE ? 0 : (int64_t)(keys[r] >> obits);
         }
         if (r < T * D) tile_min[r] = tmin[(r / D) * DP + r % D];
     }
@@ -908,6 +922,21 @@ cudaError_t launch_dom_batch(const DomBatch &b, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Key widths, known on the host: partition number (pbits bits) << obits |
+// order, with obits = bpa * d the order bits that the partition number leaves
+// below 16 (at least one per attribute). Returns obits.
+int order_bits(const gres_plan_cfg &cfg, int d, int *pbits, int *bpa) {
+    unsigned long long cells = 1;
+    if (cfg.scheme == GRES_PART_GRID || cfg.scheme == GRES_PART_ANGULAR)
+        for (int i = 0; i < (cfg.scheme == GRES_PART_GRID ? d : d - 1); i++) cells *= (unsigned long long)cfg.m;
+    if (cfg.scheme == GRES_PART_SLICED) cells = (unsigned long long)cfg.p;
+    int b = 0;
+    for (unsigned long long v = cells - 1; v; v >>= 1) b++;
+    *pbits = b;
+    *bpa = std::max(1, (16 - b) / d);
+    return *bpa * d;
+}
+
 template <int D>
 cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st) {
     const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count);
@@ -925,12 +954,9 @@ cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cuda
             pa.thr[j] = (unsigned long long)std::llround(t * t * 4294967296.0);
         }
     }
-    // key widths are known on the host: partition number << 16 | 16-bit order
-    auto bits_of = [](unsigned long long v) { int b = 0; while (v) { b++; v >>= 1; } return b; };
     auto passes = [&](int bits) { return (bits + 7) / 8; };
-    unsigned long long cells = 1;
-    if (scheme == GRES_PART_GRID || scheme == GRES_PART_ANGULAR)
-        for (int i = 0; i < (scheme == GRES_PART_GRID ? D : D - 1); i++) cells *= (unsigned long long)cfg.m;
+    int pbits = 0;
+    pa.obits = order_bits(cfg, D, &pbits, &pa.bpa);
     cudaError_t e;
     if (n <= kClusterSortMax) {
         static bool configured = false;
@@ -940,13 +966,13 @@ cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cuda
     }
     if (scheme != GRES_PART_NONE) {
         k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]); note_launch();
-        const int bits1 = scheme == GRES_PART_SLICED ? 32 : 16 + bits_of(cells - 1);
+        const int bits1 = scheme == GRES_PART_SLICED ? 32 : pa.obits + pbits;
         e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(bits1), st);
         if (e != cudaSuccess) return e;
         if (scheme == GRES_PART_SLICED) {
             k_reset_keyrange<<<1, 1, 0, st>>>(ws.hdr); note_launch();
             k_sliced_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0], ws.vals[1]); note_launch();
-            e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(16 + bits_of((unsigned long long)cfg.p - 1)), st);
+            e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(pa.obits + pbits), st);
             if (e != cudaSuccess) return e;
         }
     }
@@ -1056,13 +1082,16 @@ cudaError_t launch_load_candidates(const uint32_t *d_rows, int64_t n, int d, int
 #undef GRES_LOAD
 }
 
-cudaError_t launch_partition_out(int d, int scheme, int64_t n, Workspace &ws, int64_t *d_part,
+cudaError_t launch_partition_out(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, int64_t *d_part,
                                  uint32_t *d_order, uint32_t *d_tile_min, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
+    const int scheme = cfg.scheme;
+    int pbits = 0, bpa = 0;
+    const int obits = order_bits(cfg, d, &pbits, &bpa);
     const int64_t total = std::max<int64_t>(n, (n + kTileRows - 1) / kTileRows * d);
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)g_sm_count * 4);
 #define GRES_OUT(D) (k_partition_out<D><<<blocks, 256, 0, st>>>(ws.hdr, ws.keys[0], ws.keys[1], ws.perm, \
-                     ws.tmin, scheme, (long long)n, d_part, d_order, d_tile_min), note_launch(), cudaGetLastError())
+                     ws.tmin, scheme, obits, (long long)n, d_part, d_order, d_tile_min), note_launch(), cudaGetLastError())
     GRES_DISPATCH_D(d, GRES_OUT)
 #undef GRES_OUT
 }
