@@ -43,6 +43,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 namespace gres {
 
@@ -58,23 +59,69 @@ struct StepChunk {
     uint4 e[kStepChunk];   // (m, s1, s2, delta)
 };
 
-// Steps into device memory: division constants (m, s1, s2, divisor) and the
-// widths the pruning compares excesses with. Widths mode: the width itself.
-// Grid-parameter mode (gbits = B): the divisor is g and the width is
-// floor((2^B - 1) / g) + 1, the widest cell of floor(v g / 2^B) (clamped to
-// 2^32 - 1; that only happens at g = 1, B = 32, where every value falls in
-// one cell and nothing dominates).
-__global__ void k_upload_steps(StepChunk c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n,
+// Division constants of K widths on the device (Granlund & Montgomery; the
+// same constants as udiv_magic): magic[4j .. 4j+3] = (m, s1, s2, delta).
+__device__ __forceinline__ uint4 magic_of(uint32_t delta) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)delta) l++;
+    const unsigned long long num = (1ull << 32) * ((1ull << l) - (unsigned long long)delta);
+    return make_uint4((uint32_t)(num / delta + 1ull), l < 1 ? (uint32_t)l : 1u, l > 1 ? (uint32_t)(l - 1) : 0u, delta);
+}
+
+// Raw steps passed by value: a small chunk for the usual step lists (1 KB of
+// kernel parameters), a large one (32 KB) for long lists.
+template <int CAP>
+struct RawSteps {
+    int off;
+    int count;
+    uint32_t e[CAP];
+};
+constexpr int kRawSmall = 256;
+constexpr int kRawLarge = 8000;
+
+// Steps into device memory: division constants (m, s1, s2, divisor), made
+// here, and the widths the pruning compares excesses with. Widths mode: the
+// width itself. Grid-parameter mode (gbits = B): the divisor is g and the
+// width is floor((2^B - 1) / g) + 1, the widest cell of floor(v g / 2^B)
+// (clamped to 2^32 - 1; that only happens at g = 1, B = 32, where every value
+// falls in one cell and nothing dominates).
+template <int CAP>
+__global__ void k_upload_steps(RawSteps<CAP> c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n,
                                unsigned *zero, int gbits) {
     if (h) init_header(h, n);
     if (zero && threadIdx.x == 0) *zero = 0u;
     for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
-        const uint4 v = c.e[i];
-        unsigned long long w = v.w;
-        if (gbits) w = ((1ull << gbits) - 1ull) / v.w + 1ull;
+        const uint32_t v = c.e[i];
+        unsigned long long w = v;
+        if (gbits) w = ((1ull << gbits) - 1ull) / v + 1ull;
         steps[c.off + i] = w > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)w;
-        reinterpret_cast<uint4 *>(magic)[c.off + i] = v;
+        reinterpret_cast<uint4 *>(magic)[c.off + i] = magic_of(v);
     }
+}
+
+// Queues the uploads of k steps (the first launch also resets the header h
+// and/or clears *zero when given).
+cudaError_t upload_steps(const uint32_t *h_steps, int k, uint32_t *steps, uint32_t *magic, WsHeader *h,
+                         long long n, unsigned *zero, int gbits, cudaStream_t st) {
+    if (k <= kRawSmall) {
+        RawSteps<kRawSmall> c;
+        c.off = 0;
+        c.count = k;
+        std::memcpy(c.e, h_steps, sizeof(uint32_t) * (size_t)k);
+        k_upload_steps<kRawSmall><<<1, 256, 0, st>>>(c, steps, magic, h, n, zero, gbits); note_launch();
+        return cudaGetLastError();
+    }
+    static RawSteps<kRawLarge> c;   // 32 KB: not on the stack
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int off = 0; off < k; off += kRawLarge) {
+        c.off = off;
+        c.count = std::min(kRawLarge, k - off);
+        std::memcpy(c.e, h_steps + off, sizeof(uint32_t) * (size_t)c.count);
+        k_upload_steps<kRawLarge><<<1, 256, 0, st>>>(c, steps, magic, off == 0 ? h : nullptr, n,
+                                                     off == 0 ? zero : nullptr, gbits); note_launch();
+    }
+    return cudaGetLastError();
 }
 
 template <int D>
@@ -853,15 +900,6 @@ __global__ void k_invert_perm(const uint32_t *perm, long long S, uint32_t *iperm
         iperm[perm[i]] = (uint32_t)i;
 }
 
-// Division constants of K widths on the device (Granlund & Montgomery; the
-// same constants as udiv_magic): magic[4j .. 4j+3] = (m, s1, s2, delta).
-__device__ __forceinline__ uint4 magic_of(uint32_t delta) {
-    int l = 0;
-    while (l < 32 && (1ull << l) < (unsigned long long)delta) l++;
-    const unsigned long long num = (1ull << 32) * ((1ull << l) - (unsigned long long)delta);
-    return make_uint4((uint32_t)(num / delta + 1ull), l < 1 ? (uint32_t)l : 1u, l > 1 ? (uint32_t)(l - 1) : 0u, delta);
-}
-
 constexpr int kMaxMagicJobs = 256;
 struct MagicBatch {
     int count;
@@ -1021,35 +1059,12 @@ cudaError_t dominance_batch_d(int slots, const DomQuery *qs, int count, unsigned
 
 cudaError_t launch_upload_steps(uint32_t *d_steps, uint32_t *d_magic, unsigned *zero, const uint32_t *h_steps,
                                 int k, cudaStream_t st) {
-    StepChunk c;
-    for (int off = 0; off < k; off += kStepChunk) {
-        c.off = off;
-        c.count = std::min(kStepChunk, k - off);
-        for (int i = 0; i < c.count; i++) {
-            uint32_t m, s1, s2;
-            udiv_magic(h_steps[off + i], &m, &s1, &s2);
-            c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
-        }
-        k_upload_steps<<<1, 256, 0, st>>>(c, d_steps, d_magic, nullptr, 0, off == 0 ? zero : nullptr, 0); note_launch();
-    }
-    return cudaGetLastError();
+    return upload_steps(h_steps, k, d_steps, d_magic, nullptr, 0, zero, 0, st);
 }
 
 cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st,
                               int gbits) {
-    StepChunk c;
-    for (int off = 0; off < k; off += kStepChunk) {
-        c.off = off;
-        c.count = std::min(kStepChunk, k - off);
-        for (int i = 0; i < c.count; i++) {
-            uint32_t m, s1, s2;
-            udiv_magic(h_steps[off + i], &m, &s1, &s2);
-            c.e[i] = make_uint4(m, s1, s2, h_steps[off + i]);
-        }
-        k_upload_steps<<<1, 256, 0, st>>>(c, ws.steps, ws.magic, off == 0 ? ws.hdr : nullptr, (long long)n,
-                                          nullptr, gbits); note_launch();
-    }
-    return cudaGetLastError();
+    return upload_steps(h_steps, k, ws.steps, ws.magic, ws.hdr, (long long)n, nullptr, gbits, st);
 }
 
 cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st) {
