@@ -36,7 +36,7 @@ struct WsHeader {
     long long n_sky;              // skyline size S
     long long n_reps;             // representatives kept (mutually non-dominated)
     long long n_cand;             // representative candidates (smallest keys)
-    unsigned long long sel_thr;   // selection threshold on (f - f_min) >> sh2
+    unsigned long long sel_thr;   // level-2 selection threshold (sub-bucket)
     unsigned int sel_b1;          // level-1 selection bucket
     unsigned int sel_below;       // rows under bucket sel_b1
     unsigned int work_next;       // dynamic work counter of the gres kernel
@@ -47,7 +47,7 @@ struct WsHeader {
     unsigned int hi[kMaxD];       // per-attribute canonical maximum over the skyline
     unsigned int slo[kMaxD];      // per-attribute canonical minimum over the survivors
     unsigned int shi[kMaxD];      // per-attribute canonical maximum over the survivors
-    unsigned int pad[1];
+    unsigned int n_bnd;           // rows in the selection's boundary bucket
 };
 
 // Digit passes that do work in the radix sort of the current key range; the
@@ -98,6 +98,7 @@ __device__ __forceinline__ void init_header(WsHeader *h, long long n) {
         h->n_sky = 0;
         h->n_reps = 0;
         h->n_cand = 0;
+        h->n_bnd = 0;
         h->work_next = 0;
         h->status = 0;
         h->sorted_sel = 0;

@@ -139,50 +139,37 @@ __device__ __forceinline__ void warp_minmax_atomic(unsigned long long kmin, unsi
     }
 }
 
-template <int D>
-__global__ void k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys, WsHeader *h) {
-    unsigned long long kmin = ~0ull, kmax = 0ull;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        uint32_t x[D];
-        load_canon<D>(data, i, dir, x);
-        unsigned long long k = 0;
-        #pragma unroll
-        for (int j = 0; j < D; j++) k += x[j];
-        keys[i] = k;
-        kmin = k < kmin ? k : kmin;
-        kmax = k > kmax ? k : kmax;
-    }
-    warp_minmax_atomic(kmin, kmax, h);
-}
-
 // ---- representative selection ------------------------------------------------
-// Level 1 buckets f - f_min by its top 12 bits (shift sh1); level 2 splits the
-// bucket where the count passes R by the next (up to 12) bits (shift sh2).
+// The representatives are the rows of smallest f (at most R of them, Sec. 3.1),
+// found by two histogram levels. Level 1 buckets f without knowing its range:
+// f < 128 exactly, larger f by its leading bit and the 6 bits below it (1,920
+// buckets, monotone in f, relative width 1/64). Level 2 splits the bucket
+// where the running count passes R into up to 4,096 equal sub-buckets.
 constexpr int kSelBuckets = 4096;
 
-__device__ __forceinline__ int sel_shift1(const WsHeader *h) {
-    const unsigned long long range = h->key_max >= h->key_min ? h->key_max - h->key_min : 0ull;
-    const int bits = range ? 64 - __clzll((long long)range) : 0;
-    return bits > 12 ? bits - 12 : 0;
+__device__ __forceinline__ uint32_t fbucket(unsigned long long f) {
+    if (f < 128ull) return (uint32_t)f;
+    const int e = 63 - __clzll((long long)f);                  // leading bit, 7 .. 34
+    return 128u + (uint32_t)(e - 7) * 64u + (uint32_t)((f >> (e - 6)) & 63ull);
 }
 
-// Run by the last block of k_sel_hist (1024 threads): first bucket at which
-// the running count (plus
-// `below` for level 2) exceeds R. Level 1 writes sel_b1 and sel_below (the
-// count under bucket b1; sel_b1 = 4096 when every row fits); level 2 writes
-// the final threshold sel_thr in units of 2^sh2 (rows with
-// (f - f_min) >> sh2 < sel_thr are representatives: at most R of them).
-__device__ __forceinline__ void sel_find(const uint32_t *hist, int level, int R, WsHeader *h) {
+// Lowest value of level-1 bucket b and log2 of its width.
+__device__ __forceinline__ void fbucket_range(uint32_t b, unsigned long long *lo, int *wbits) {
+    if (b < 128u) { *lo = b; *wbits = 0; return; }
+    const int e = 7 + (int)((b - 128u) / 64u);
+    const unsigned long long m = (b - 128u) % 64u;
+    *wbits = e - 6;
+    *lo = (64ull + m) << (e - 6);
+}
+
+// Run by the last block (1024 threads) of a histogram kernel: the first bucket
+// at which the running count (plus `base`) exceeds R, as (bucket << 32 |
+// count below it); ~0 when every row fits.
+__device__ __forceinline__ unsigned long long sel_find(const uint32_t *hist, uint32_t base, int R) {
     __shared__ uint32_t wsum[32];
     __shared__ unsigned long long found;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (level == 2 && h->sel_b1 >= (unsigned)kSelBuckets) {
-        if (tid == 0) h->sel_thr = ~0ull;
-        return;
-    }
     if (tid == 0) found = ~0ull;
-    const uint32_t base = level == 1 ? 0u : h->sel_below;
     uint32_t c[4], local = 0;
     #pragma unroll
     for (int q = 0; q < 4; q++) { c[q] = hist[4 * tid + q]; local += c[q]; }
@@ -206,55 +193,81 @@ __device__ __forceinline__ void sel_find(const uint32_t *hist, int level, int R,
         run += c[q];
     }
     __syncthreads();
-    if (tid == 0) {
-        const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
-        if (level == 1) {
+    return found;
+}
+
+// Sum keys f = sum_i c_i (A2) and the level-1 histogram; the last block picks
+// the level-1 bucket b1 (sel_b1 = kSelBuckets when all rows fit in R).
+template <int D>
+__global__ void __launch_bounds__(1024)
+k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys, WsHeader *h, uint32_t *hist, int R) {
+    __shared__ uint32_t sh[kSelBuckets];
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        uint32_t x[D];
+        load_canon<D>(data, i, dir, x);
+        unsigned long long k = 0;
+        #pragma unroll
+        for (int j = 0; j < D; j++) k += x[j];
+        keys[i] = k;
+        atomicAdd(&sh[fbucket(k)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    if (last_block_done(&h->done[0])) {
+        const unsigned long long found = sel_find(hist, 0u, R);
+        if (threadIdx.x == 0) {
             if (found == ~0ull) { h->sel_b1 = kSelBuckets; h->sel_below = 0; }
             else { h->sel_b1 = (uint32_t)(found >> 32); h->sel_below = (uint32_t)found; }
-        } else {
-            const unsigned long long b2 = found == ~0ull ? (1ull << (sh1 - sh2)) : (found >> 32);
-            h->sel_thr = ((unsigned long long)h->sel_b1 << (sh1 - sh2)) + b2;
         }
     }
 }
 
+// Level 2 and the gather in one pass: rows below bucket b1 are representatives
+// at once; rows in b1 are counted per sub-bucket and listed (boundary list,
+// capacity n). The last block finds the sub-bucket threshold and adds the
+// listed rows under it. At most R rows in all.
 __global__ void __launch_bounds__(1024)
-k_sel_hist(const unsigned long long *keys, long long n, WsHeader *h, int level, uint32_t *hist, int R) {
+k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *hist, int R,
+         unsigned long long *bnd, uint32_t *rep_idx) {
     __shared__ uint32_t sh[kSelBuckets];
     for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
     __syncthreads();
-    const unsigned long long kmin = h->key_min;
-    const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
-    const unsigned long long b1 = h->sel_b1;
-    const bool active = level == 1 || b1 < kSelBuckets;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; active && i < n;
+    const uint32_t b1 = h->sel_b1;
+    unsigned long long lo = 0;
+    int wbits = 0;
+    if (b1 < (uint32_t)kSelBuckets) fbucket_range(b1, &lo, &wbits);
+    const int sh2 = wbits > 12 ? wbits - 12 : 0;
+    unsigned *n_cand = reinterpret_cast<unsigned *>(&h->n_cand);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long kn = keys[i] - kmin;
-        if (level == 1) {
-            atomicAdd(&sh[kn >> sh1], 1u);
-        } else if ((kn >> sh1) == b1) {
-            atomicAdd(&sh[(kn >> sh2) & ((1ull << (sh1 - sh2)) - 1ull)], 1u);
+        const unsigned long long f = keys[i];
+        const uint32_t b = fbucket(f);
+        if (b < b1) {
+            const unsigned pos = atomicAdd(n_cand, 1u);
+            if (pos < (unsigned)kMaxReps) rep_idx[pos] = (uint32_t)i;
+        } else if (b == b1) {
+            const uint32_t sb = (uint32_t)((f - lo) >> sh2);
+            atomicAdd(&sh[sb], 1u);
+            bnd[atomicAdd(&h->n_bnd, 1u)] = ((unsigned long long)sb << 32) | (unsigned long long)i;
         }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
         if (sh[b]) atomicAdd(&hist[b], sh[b]);
-    if (last_block_done(&h->done[0])) sel_find(hist, level, R, h);
-}
-
-// Rows under the threshold, appended in any order (sorted next).
-__global__ void k_sel_gather(const unsigned long long *keys, long long n, WsHeader *h,
-                             unsigned long long *rep_key, uint32_t *rep_idx) {
-    const unsigned long long kmin = h->key_min, thr = h->sel_thr;
-    const int sh1 = sel_shift1(h), sh2 = sh1 > 12 ? sh1 - 12 : 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long kn = keys[i] - kmin;
-        if ((kn >> sh2) < thr) {
-            const unsigned pos = atomicAdd(reinterpret_cast<unsigned *>(&h->n_cand), 1u);
-            if (pos < (unsigned)kMaxReps) {
-                rep_key[pos] = keys[i];
-                rep_idx[pos] = (uint32_t)i;
+    if (last_block_done(&h->done[1])) {
+        if (b1 >= (uint32_t)kSelBuckets) return;   // every row is a representative
+        const unsigned long long found = sel_find(hist, h->sel_below, R);
+        const unsigned long long thr = found == ~0ull ? ~0ull : (found >> 32);
+        const unsigned nb = h->n_bnd;
+        for (unsigned j = threadIdx.x; j < nb; j += blockDim.x) {
+            const unsigned long long v = bnd[j];
+            if ((v >> 32) < thr) {
+                const unsigned pos = atomicAdd(n_cand, 1u);
+                if (pos < (unsigned)kMaxReps) rep_idx[pos] = (uint32_t)(v & 0xFFFFFFFFull);
             }
         }
     }
@@ -271,8 +284,8 @@ __global__ void k_sel_gather(const unsigned long long *keys, long long n, WsHead
 // counts (nb of them).
 template <int D>
 __global__ void __launch_bounds__(kMaxReps)
-k_rep_sort(const uint32_t *data, int dir, const unsigned long long *rep_key, const uint32_t *rep_idx,
-           WsHeader *h, uint32_t *rows, uint32_t *blocksum, long long nb) {
+k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, uint32_t *rows,
+           uint32_t *blocksum, long long nb) {
     __shared__ unsigned long long sk[kMaxReps];
     __shared__ uint32_t lo[D], hi[D];
     const int tid = threadIdx.x;
@@ -408,10 +421,10 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
 
 // Survivors in input order: canonical rows, original row numbers, and their
 // per-attribute range (slo / shi) for the spatial order. With `clear`, the
-// flags read are reset to 0 for k_final.
+// flags read and the block's segment offset are reset to 0 for k_final.
 template <int D>
 __global__ void __launch_bounds__(kCT)
-k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, const uint32_t *blocksum,
+k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, uint32_t *blocksum,
                uint32_t *surv_rows, uint32_t *surv_orig, WsHeader *h, int clear) {
     __shared__ uint32_t blo[D], bhi[D];
     if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
@@ -451,6 +464,7 @@ k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, cons
         atomicMin(&h->slo[threadIdx.x], blo[threadIdx.x]);
         atomicMax(&h->shi[threadIdx.x], bhi[threadIdx.x]);
     }
+    if (clear && threadIdx.x == 0) blocksum[blockIdx.x] = 0u;   // k_final counts skyline rows here
 }
 
 // Sort keys of the survivors: a 16-bit Morton code over their range. Also
@@ -542,11 +556,12 @@ k_gather_tiles(const uint32_t *surv_rows, const uint32_t *surv_orig, const uint3
 // attribute -- the grid-dominance pruning of Sec. 3.1 on tiles. One warp per
 // survivor: lanes test 32 super-tile minima, then the 32 tile minima of each
 // possible super-tile, then the 32 rows of each possible tile, stopping at the
-// first dominator. Sets skyflag[original row].
+// first dominator. Sets skyflag[original row] and, with segcount, counts the
+// skyline rows of each kCB-row segment.
 template <int D>
 __global__ void __launch_bounds__(kTriThreads)
 k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const uint32_t *smin,
-        const WsHeader *h, uint32_t *skyflag) {
+        const WsHeader *h, uint32_t *skyflag, uint32_t *segcount) {
     const long long M = h->n_surv;
     const long long T = (M + kTileRows - 1) / kTileRows;
     const long long T2 = (T + 31) / 32;
@@ -589,7 +604,11 @@ k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const 
                 }
             }
         }
-        if (!dom && lane == 0) skyflag[orig[q]] = 1u;
+        if (!dom && lane == 0) {
+            const uint32_t o = orig[q];
+            skyflag[o] = 1u;
+            if (segcount) atomicAdd(&segcount[o / kCB], 1u);
+        }
     }
 }
 
@@ -617,14 +636,31 @@ k_count_flags(const uint32_t *flags, long long n, uint32_t *blocksum, long long 
 template <int D>
 __global__ void __launch_bounds__(kCT)
 k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyflag,
-              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows, WsHeader *h) {
+              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows, WsHeader *h, long long nb_raw) {
     __shared__ uint32_t blo[D], bhi[D];
     if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
     if (blockIdx.x == 0 && threadIdx.x == 0) { h->key_min = ~0ull; h->key_max = 0ull; }
     uint32_t lo[D], hi[D];
     #pragma unroll
     for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
-    uint32_t run = blocksum[blockIdx.x];
+    uint32_t run;
+    if (nb_raw) {
+        // raw per-segment counts (from k_final): this block's offset is the sum of the
+        // counts before it, S the sum of all
+        uint32_t before = 0, all = 0;
+        for (long long j = threadIdx.x; j < nb_raw; j += kCT) {
+            const uint32_t c = blocksum[j];
+            before += j < (long long)blockIdx.x ? c : 0u;
+            all += c;
+        }
+        uint32_t tb, ta;
+        block_scan(before, &tb);
+        block_scan(all, &ta);
+        run = tb;
+        if (blockIdx.x == 0 && threadIdx.x == 0) h->n_sky = ta;
+    } else {
+        run = blocksum[blockIdx.x];
+    }
     const long long b0 = (long long)blockIdx.x * kCB;
     #pragma unroll 1
     for (int r = 0; r < kPer; r++) {
@@ -754,15 +790,13 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
                       int64_t *d_sky_idx, cudaStream_t st) {
     const long long nb = (n + kCB - 1) / kCB;
     const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 4);
-    k_keys<D><<<gb, 256, 0, st>>>(d_data, n, dir, ws.keys[0], ws.hdr); note_launch();
     cudaError_t e = cudaMemsetAsync(ws.sel_hist, 0, sizeof(uint32_t) * 2 * kSelBuckets, st);
     if (e != cudaSuccess) return e;
     const int hb = (int)std::min<long long>((n + 1023) / 1024, 152LL * 2);
-    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 1, ws.sel_hist, reps); note_launch();
-    k_sel_hist<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, 2, ws.sel_hist + kSelBuckets, reps); note_launch();
-    k_sel_gather<<<gb, 256, 0, st>>>(ws.keys[0], n, ws.hdr, ws.rep_key, ws.rep_idx); note_launch();
-    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_key, ws.rep_idx, ws.hdr, ws.reps, ws.blocksum,
-                                          nb); note_launch();
+    k_keys<D><<<hb, 1024, 0, st>>>(d_data, n, dir, ws.keys[0], ws.hdr, ws.sel_hist, reps); note_launch();
+    k_sel_l2<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, ws.sel_hist + kSelBuckets, reps, ws.keys[1],
+                                  ws.rep_idx); note_launch();
+    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_idx, ws.hdr, ws.reps, ws.blocksum, nb); note_launch();
     static int filter_blocks = 0;   // resident blocks of k_filter<D> on this GPU
     if (filter_blocks == 0) {
         int per_sm = 0, dev = 0, sms = 0;
@@ -790,10 +824,12 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
                                                            ws.hdr, ws.cand, ws.perm, ws.tmin, ws.smin); note_launch();
     }
     k_final<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
-        ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags); note_launch();
-    k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum, nb, ws.hdr); note_launch();
+        ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags, small ? ws.blocksum : nullptr); note_launch();
+    if (!small) {
+        k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum, nb, ws.hdr); note_launch();
+    }
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
-                                                    ws.sky_rows, ws.hdr); note_launch();
+                                                    ws.sky_rows, ws.hdr, small ? nb : 0); note_launch();
     return cudaGetLastError();
 }
 
