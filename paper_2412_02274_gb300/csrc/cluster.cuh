@@ -242,6 +242,105 @@ __device__ __forceinline__ void cluster_radix_sort(cg::cluster_group &cl, uint32
     }
 }
 
+// ---- the same sort with the data in the cluster's shared memory -------------
+// For n <= kClCTAs * kClSmemCap items with 32-bit keys. CTA r holds positions
+// [r c, r c + c) of the current order (c = ceil(n / C) rounded up to 32) in
+// its buffers kb[cur] / vb[cur]; a pass scatters each item straight into the
+// buffer of the CTA that owns its new position (distributed shared memory), so
+// the passes touch no global memory. Ranks, bases and barriers as in
+// cluster_radix_sort. Returns the buffer (0 / 1) holding the result.
+constexpr int kClSmemCap = 8192;
+// dynamic shared memory: the sort's words plus two (key, value) buffers
+constexpr size_t kClSmemBytes = kClSortBytes + sizeof(uint32_t) * 4 * (size_t)kClSmemCap;
+
+__device__ __forceinline__ long long cluster_chunk(long long n) {
+    return (((n + kClCTAs - 1) / kClCTAs) + 31) & ~31LL;
+}
+
+__device__ __forceinline__ int cluster_radix_sort_smem(cg::cluster_group &cl, uint32_t *sm, uint32_t *kb0,
+                                                       uint32_t *vb0, uint32_t *kb1, uint32_t *vb1, long long n,
+                                                       uint32_t kmin, int passes, int cur) {
+    uint32_t *hist = sm;                      // 256
+    uint32_t *base = sm + 256;                // 256
+    uint32_t *wsum = sm + 512;                // kClWarps
+    uint32_t *wcnt = sm + 512 + kClWarps;     // kClWarps x 256
+    uint32_t *woff = wcnt + kClWarps * 256;   // kClWarps x 256
+    const int r = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long c = cluster_chunk(n);
+    const long long b0 = min(n, (long long)r * c);
+    const int cnt = (int)(min(n, b0 + c) - b0);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int pass = 0; pass < passes; pass++) {
+        const uint32_t *kin = cur ? kb1 : kb0, *vin = cur ? vb1 : vb0;
+        const int shift = 8 * pass;
+        if (tid < 256) hist[tid] = 0;
+        for (int j = tid; j < kClWarps * 256; j += kClThreads) wcnt[j] = 0;
+        __syncthreads();
+        for (int i = tid; i < cnt; i += kClThreads) atomicAdd(&hist[((kin[i] - kmin) >> shift) & 255u], 1u);
+        cl.sync();
+        if (tid < 256) {
+            uint32_t tot = 0, pre = 0;
+            #pragma unroll
+            for (int q = 0; q < kClCTAs; q++) {
+                const uint32_t v = cl.map_shared_rank(hist, q)[tid];
+                tot += v;
+                pre += q < r ? v : 0u;
+            }
+            uint32_t incl = tot;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) wsum[w] = incl;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            uint32_t before = 0;
+            #pragma unroll
+            for (int j = 0; j < 8; j++) before += j < w ? wsum[j] : 0u;
+            base[tid] = before + incl - tot + pre;
+        }
+        __syncthreads();
+        uint32_t *kout = cur ? kb0 : kb1, *vout = cur ? vb0 : vb1;
+        for (int r0 = 0; r0 < cnt; r0 += kClThreads) {
+            const int i = r0 + tid;
+            const bool valid = i < cnt;
+            uint32_t key = 0, val = 0, dg = 256;  // invalid items share a digit no real item has
+            if (valid) {
+                key = kin[i];
+                val = vin[i];
+                dg = ((key - kmin) >> shift) & 255u;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, dg);
+            const uint32_t rank = __popc(peers & lt_mask);
+            if (valid && rank == 0) wcnt[w * 256 + dg] = __popc(peers);
+            __syncthreads();
+            if (tid < 256) {
+                uint32_t run = base[tid];
+                #pragma unroll 8
+                for (int j = 0; j < kClWarps; j++) {
+                    const uint32_t v = wcnt[j * 256 + tid];
+                    wcnt[j * 256 + tid] = 0;
+                    woff[j * 256 + tid] = run;
+                    run += v;
+                }
+                base[tid] = run;
+            }
+            __syncthreads();
+            if (valid) {
+                const uint32_t pos = woff[w * 256 + dg] + rank;
+                const int owner = (int)(pos / (uint32_t)c);
+                const uint32_t li = pos - (uint32_t)owner * (uint32_t)c;
+                cl.map_shared_rank(kout, owner)[li] = key;
+                cl.map_shared_rank(vout, owner)[li] = val;
+            }
+        }
+        cl.sync();
+        cur ^= 1;
+    }
+    return cur;
+}
+
 // Launches a cluster kernel: one cluster of kClCTAs CTAs (the helpers above
 // assume exactly that many), kClThreads threads,
 // `smem` bytes of dynamic shared memory (the kernel's limit is raised on first

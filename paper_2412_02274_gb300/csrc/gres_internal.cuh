@@ -225,8 +225,9 @@ cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
 // Uploads the widths and their division constants and resets the header.
 cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st,
                               int gbits = 0);
-// Sorts of at most kClusterSortMax items run as one launch of one thread-block
-// cluster; larger ones as three kernels per digit pass.
+// Inputs of at most kClusterSortMax rows sort their survivors and their
+// skyline inside one thread-block cluster per sort (cluster.cuh); larger ones
+// with three grid-wide kernels per digit pass (launch_radix_sort).
 constexpr int64_t kClusterSortMax = 131072;
 cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
                               int max_passes, cudaStream_t st);

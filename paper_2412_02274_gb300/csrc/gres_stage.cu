@@ -172,6 +172,7 @@ struct PartArgs {
     int dim;         // SLICED attribute
     int bpa;         // bits per attribute of the order inside a partition
     int obits;       // bpa * D: the key is partition << obits | order
+    int key32;       // every key fits 32 bits (the sort can stay in shared memory)
     unsigned long long thr[64];   // ANGULAR: tan^2(j pi / 2m) * 2^32, j = 1 .. m-1
 };
 
@@ -427,8 +428,55 @@ k_part_cluster(const uint32_t *sky_rows, WsHeader *h, PartArgs a, unsigned long 
     const long long S = h->n_sky;
     const bool none = a.scheme == GRES_PART_NONE;
     int sel = 0;
-    if (!none) {
-        // first key: partition number << 16 | Morton code (SLICED: the chosen attribute)
+    if (!none && a.key32) {
+        // keys of at most 32 bits: the (key, skyline position) pairs stay in the cluster's
+        // shared memory, CTA r holding positions [b0, b0 + cnt)
+        uint32_t *kb0 = sm + kClSortWords, *vb0 = kb0 + kClSmemCap, *kb1 = vb0 + kClSmemCap, *vb1 = kb1 + kClSmemCap;
+        const long long c = cluster_chunk(S);
+        const long long b0 = min(S, (long long)r * c);
+        const int cnt = (int)(min(S, b0 + c) - b0);
+        if (threadIdx.x == 0) { kr[0] = ~0ull; kr[1] = 0ull; }
+        __syncthreads();
+        unsigned long long kmn = ~0ull, kmx = 0ull;
+        for (int i = threadIdx.x; i < cnt; i += kClThreads) {
+            const unsigned long long key = part_key<D>(sky_rows, b0 + i, h, a);
+            kb0[i] = (uint32_t)key;
+            vb0[i] = (uint32_t)(b0 + i);
+            kmn = key < kmn ? key : kmn;
+            kmx = key > kmx ? key : kmx;
+        }
+        cta_key_add(kmn, kmx, kr);
+        unsigned long long kmin, kmax;
+        cluster_key_range(cl, kr, &kmin, &kmax);
+        int cur = cluster_radix_sort_smem(cl, sm, kb0, vb0, kb1, vb1, S, (uint32_t)kmin, key_passes(kmin, kmax), 0);
+        if (a.scheme == GRES_PART_SLICED) {
+            // rank q -> slice floor(q p / S); re-key in place, sort again
+            __shared__ unsigned long long kr2[2];
+            if (threadIdx.x == 0) { kr2[0] = ~0ull; kr2[1] = 0ull; }
+            __syncthreads();
+            uint32_t *kc = cur ? kb1 : kb0;
+            const uint32_t *vc = cur ? vb1 : vb0;
+            kmn = ~0ull;
+            kmx = 0ull;
+            for (int i = threadIdx.x; i < cnt; i += kClThreads) {
+                const unsigned long long key = sliced_key<D>(sky_rows, vc[i], b0 + i, S, h, a);
+                kc[i] = (uint32_t)key;
+                kmn = key < kmn ? key : kmn;
+                kmx = key > kmx ? key : kmx;
+            }
+            cta_key_add(kmn, kmx, kr2);
+            cluster_key_range(cl, kr2, &kmin, &kmax);
+            cur = cluster_radix_sort_smem(cl, sm, kb0, vb0, kb1, vb1, S, (uint32_t)kmin, key_passes(kmin, kmax), cur);
+        }
+        // the order (and keys) to global memory for the candidate layout
+        const uint32_t *kf = cur ? kb1 : kb0, *vf = cur ? vb1 : vb0;
+        for (int i = threadIdx.x; i < cnt; i += kClThreads) {
+            k0[b0 + i] = kf[i];
+            v0[b0 + i] = vf[i];
+        }
+        cl.sync();
+    } else if (!none) {
+        // first key: partition number << obits | order (SLICED: the chosen attribute)
         if (threadIdx.x == 0) { kr[0] = ~0ull; kr[1] = 0ull; }
         __syncthreads();
         unsigned long long kmn = ~0ull, kmx = 0ull;
@@ -995,10 +1043,11 @@ cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cuda
     auto passes = [&](int bits) { return (bits + 7) / 8; };
     int pbits = 0;
     pa.obits = order_bits(cfg, D, &pbits, &pa.bpa);
+    pa.key32 = pbits + pa.obits <= 32 ? 1 : 0;   // SLICED's first key is one 32-bit value
     cudaError_t e;
     if (n <= kClusterSortMax) {
         static bool configured = false;
-        return launch_cluster(k_part_cluster<D>, kClSortBytes, &configured, st, (const uint32_t *)ws.sky_rows,
+        return launch_cluster(k_part_cluster<D>, kClSmemBytes, &configured, st, (const uint32_t *)ws.sky_rows,
                               ws.hdr, pa, ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], ws.cand, ws.tmin,
                               ws.smin, ws.perm);
     }

@@ -14,7 +14,7 @@
 // ranks its items per digit in input order (warp match_any for ranks within a
 // warp, a per-digit prefix over warps for the block, a running per-digit carry
 // across the block's rounds).
-#include "cluster.cuh"
+#include "gres_internal.cuh"
 
 namespace gres {
 
@@ -173,35 +173,15 @@ k_scatter(WsHeader *h, const unsigned long long *keys_in, const uint32_t *vals_i
     }
 }
 
-// ---- one-launch sort for small inputs: one thread-block cluster -------------
-// All passes in one launch (cluster_radix_sort, cluster.cuh); the pass count
-// comes from the device-side key range as in the three-kernel form.
-__global__ void __launch_bounds__(kClThreads)
-k_sort_cluster(WsHeader *h, unsigned long long *k0, uint32_t *v0, unsigned long long *k1, uint32_t *v1,
-               const long long *d_n, int max_passes) {
-    extern __shared__ uint32_t sm[];
-    cg::cluster_group cl = cg::this_cluster();
-    const int all = radix_passes(h);
-    if (cl.block_rank() == 0 && threadIdx.x == 0) h->sorted_sel = (unsigned)(all & 1);
-    cluster_radix_sort(cl, sm, k0, v0, k1, v1, *d_n, h->key_min, all < max_passes ? all : max_passes);
-}
-
 }  // namespace
 
 int64_t sort_blocks(int64_t n) { return (n + kTile - 1) / kTile; }
-
-cudaError_t launch_sort_cluster(Workspace &ws, const long long *d_n, int max_passes, cudaStream_t st) {
-    static bool configured = false;
-    return launch_cluster(k_sort_cluster, kClSortBytes, &configured, st, ws.hdr, ws.keys[0], ws.vals[0],
-                          ws.keys[1], ws.vals[1], d_n, max_passes);
-}
 
 // Queues up to `max_passes` digit passes on ws.keys[0]/ws.vals[0] (count in
 // *d_n, at most n_max). The sorted data ends in buffer hdr->sorted_sel.
 cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
                               int max_passes, cudaStream_t st) {
     if (n_max <= 0) return cudaSuccess;
-    if (n_max <= kClusterSortMax) return launch_sort_cluster(ws, d_n, max_passes, st);
     const int64_t G = sort_blocks(n_max);
     if (G > 0) {
         for (int p = 0; p < max_passes; p++) {

@@ -714,28 +714,35 @@ k_surv_cluster(Workspace ws) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const long long tt = (long long)C * kClThreads, gt = (long long)r * kClThreads + tid;
     WsHeader *h = ws.hdr;
-    const long long M = h->n_surv;
+    const long long M = h->n_surv;   // <= n <= kClCTAs * kClSmemCap
     if (tid == 0) { kr[0] = ~0ull; kr[1] = 0ull; }
     __syncthreads();
+    // this CTA's positions [b0, b0 + cnt) of the (key, survivor) pairs, in shared memory
+    uint32_t *kb0 = sm + kClSortWords, *vb0 = kb0 + kClSmemCap, *kb1 = vb0 + kClSmemCap, *vb1 = kb1 + kClSmemCap;
+    const long long c = cluster_chunk(M);
+    const long long b0 = min(M, (long long)r * c);
+    const int cnt = (int)(min(M, b0 + c) - b0);
     const int bits = 16 / D;
     unsigned long long kmn = ~0ull, kmx = 0ull;
-    for (long long j = gt; j < M; j += tt) {
+    for (int i = tid; i < cnt; i += kClThreads) {
         uint32_t x[D];
-        load_row<D>(ws.surv_rows, j, x);
-        const unsigned long long k = morton<D>(x, h->slo, h->shi, bits);
-        ws.keys[0][j] = k;
-        ws.vals[0][j] = (uint32_t)j;
+        load_row<D>(ws.surv_rows, b0 + i, x);
+        const uint32_t k = morton<D>(x, h->slo, h->shi, bits);
+        kb0[i] = k;
+        vb0[i] = (uint32_t)(b0 + i);
         kmn = k < kmn ? k : kmn;
         kmx = k > kmx ? k : kmx;
     }
     cta_key_add(kmn, kmx, kr);
     unsigned long long kmin, kmax;
     cluster_key_range(cl, kr, &kmin, &kmax);
-    const int passes = key_passes(kmin, kmax);
-    cluster_radix_sort(cl, sm, ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], M, kmin, passes);
-    const uint32_t *vals = ws.vals[passes & 1];
+    const int fin = cluster_radix_sort_smem(cl, sm, kb0, vb0, kb1, vb1, M, (uint32_t)kmin, key_passes(kmin, kmax), 0);
+    // the sorted survivor numbers to global memory for the tile gather
+    const uint32_t *vf = fin ? vb1 : vb0;
+    for (int i = tid; i < cnt; i += kClThreads) ws.vals[0][b0 + i] = vf[i];
+    cl.sync();
+    const uint32_t *vals = ws.vals[0];
     // survivor tiles in key order: one super-tile per CTA and round, warp w builds its tile w
     const long long T = (M + kTileRows - 1) / kTileRows;
     const long long T2 = (T + 31) / 32;
@@ -781,7 +788,7 @@ k_surv_cluster(Workspace ws) {
         }
         __syncthreads();
     }
-    if (r == 0 && tid == 0) h->sorted_sel = (unsigned)(passes & 1);
+    if (r == 0 && tid == 0) h->sorted_sel = 0u;
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
@@ -813,7 +820,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
                                                      ws.surv_orig, ws.hdr, small ? 1 : 0); note_launch();
     if (small) {
         static bool configured = false;
-        e = launch_cluster(k_surv_cluster<D>, kClSortBytes, &configured, st, ws);
+        e = launch_cluster(k_surv_cluster<D>, kClSmemBytes, &configured, st, ws);
         if (e != cudaSuccess) return e;
     } else {
         k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
