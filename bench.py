@@ -604,11 +604,46 @@ def run_sweep(args):
             print(json.dumps({"row": rows[-1]}), file=sys.stderr, flush=True)
         del x, ws
         torch.cuda.empty_cache()
+    # Representative Filtering inside the gres stage (32 representatives), against the plain search
+    ablation = []
+    for dist, n, d in (("ant", 1_000_000, 3), ("ant", 1_000_000, 5), ("uni", 1_000_000, 6),
+                       ("ant", 100_000, 4)):
+        data = make_dataset(dist, n, d, bits=20, seed=0)
+        x = G.to_device_u32(data, dev)
+        ws = G.alloc_workspace(n, d, len(glist))
+        for scheme in ("grid", "sliced"):
+            mp, cells = table1_plan(scheme, d, 16)
+            kw = {"m": mp} if scheme == "grid" else {"p": mp}
+            for reps_on in (False, True):
+                cfg = G.plan(SCHEMES[scheme], gres_reps=reps_on, **kw)
+                G.gres_compute_g(x, 20, glist, G.MIN, cfg, ws=ws, stream=stream)
+                tests = torch.zeros(2, dtype=torch.int64, device=dev)
+                G.gres_compute_g(x, 20, glist, G.MIN, G.plan(SCHEMES[scheme], gres_reps=reps_on, count_tests=True, **kw),
+                                 ws=ws, stream=stream, tests=tests)
+                lane_tests, checks = (int(v) for v in tests.cpu().tolist())
+                G.timing_enable(True)
+                G.timing_read()
+                t = []
+                for _ in range(3):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    G.gres_compute_g(x, 20, glist, G.MIN, cfg, ws=ws, stream=stream)
+                    b.record(stream)
+                    b.synchronize()
+                    t.append(a.elapsed_time(b))
+                st = G.timing_read()
+                G.timing_enable(False)
+                ablation.append({"dist": dist, "n": n, "d": d, "scheme": scheme, "gres_reps": 32 if reps_on else 0,
+                                 "lane_tests": lane_tests, "pruning_checks": checks, "ms": float(np.median(t)),
+                                 "dominance_ms": st["dominance"][0] / max(st["dominance"][1], 1)})
+                print(json.dumps({"ablation": ablation[-1]}), file=sys.stderr, flush=True)
+        del x, ws
+        torch.cuda.empty_cache()
     line = {"metric": "dominance tests and time per scheme (Table 1 sweep)", "value": len(rows),
             "unit": "configurations", "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": {"workload": "sweep", "g": "25..2", "value_bits": 20,
-                                            "seed": 0}, "rows": rows}
+                                            "seed": 0}, "rows": rows, "gres_reps_ablation": ablation}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -93,6 +93,15 @@ typedef struct {
 /* Count the dominance tests and pruning checks the gres kernel evaluates into
  * d_tests (see gres_compute). For accounting only. */
 #define GRES_FLAG_COUNT_TESTS 1
+/* Representative Filtering in the gres stage (Sec. 3.1, applied to gres; the
+ * paper reports it of little use there): before its search, every skyline
+ * tuple is tested at every step against the 32 rows of smallest f (sum of the
+ * values; by stability any rows of r may serve as candidates), and the first
+ * step at which one of them dominates bounds the search. Results are
+ * unchanged. Honoured by gres_compute and gres_compute_g (rejected by the
+ * dataset, batch and server calls). With GRES_FLAG_COUNT_TESTS the
+ * representative tests are counted in d_tests[0] too. */
+#define GRES_FLAG_GRES_REPS 2
 
 /* Thread-local message for the calling thread's most recent failed call
  * ("" if none). The pointer stays valid until the next call on that thread. */

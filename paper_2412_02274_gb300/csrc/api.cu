@@ -69,7 +69,7 @@ gres_status check_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *out) 
     if (c.scheme < GRES_PART_NONE || c.scheme > GRES_PART_SLICED)
         return fail(GRES_EINVAL, "cfg.scheme must be a gres_part");
     if (c.reserved != 0) return fail(GRES_EINVAL, "cfg.reserved must be 0");
-    if (c.flags & ~GRES_FLAG_COUNT_TESTS) return fail(GRES_EINVAL, "unknown cfg.flags bits");
+    if (c.flags & ~(GRES_FLAG_COUNT_TESTS | GRES_FLAG_GRES_REPS)) return fail(GRES_EINVAL, "unknown cfg.flags bits");
     if (c.reps == 0) c.reps = gres::kMaxReps;
     if (c.reps < 1 || c.reps > gres::kMaxReps) return fail(GRES_EINVAL, "cfg.reps must be in [1, 1024]");
     if (c.slots == 0) c.slots = 8;
@@ -204,6 +204,7 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.smin = static_cast<uint32_t *>(take(4 * DP * (tiles / 32 + 1)));
     w.perm = static_cast<uint32_t *>(take(4 * nn));
     w.res = static_cast<int32_t *>(take(4 * nn));
+    w.greps = static_cast<uint32_t *>(take(4 * DP * 32));
     w.steps = static_cast<uint32_t *>(take(4 * (size_t)(k > 0 ? k : 1)));
     w.magic = static_cast<uint32_t *>(take(16 * (size_t)(k > 0 ? k : 1)));
     w.bytes = off;
@@ -308,7 +309,8 @@ gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t d
     cudaError_t e = gres::launch_init_steps(ws, n, h_steps, k, st);
     if (e != cudaSuccess) return cuda_fail(e, "init");
     gres::stage_begin(gres::kStageSkyline, st);
-    e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st);
+    e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st,
+                             (plan.flags & GRES_FLAG_GRES_REPS) != 0);
     gres::stage_end(gres::kStageSkyline, st);
     if (e != cudaSuccess) return cuda_fail(e, "skyline");
     e = gres::launch_gres_stage(d_data, n, d, dir, k, plan, ws, d_sky_idx, d_step_idx, d_tests, st);
@@ -344,7 +346,8 @@ gres_status gres_compute_g(const uint32_t *d_data, int64_t n, int32_t d, int32_t
     cudaError_t e = gres::launch_init_steps(ws, n, h_g, k, st, bits);
     if (e != cudaSuccess) return cuda_fail(e, "init");
     gres::stage_begin(gres::kStageSkyline, st);
-    e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st);
+    e = gres::launch_skyline(d_data, n, d, dir, plan.reps, ws, d_sky_idx, st,
+                             (plan.flags & GRES_FLAG_GRES_REPS) != 0);
     gres::stage_end(gres::kStageSkyline, st);
     if (e != cudaSuccess) return cuda_fail(e, "skyline");
     e = gres::launch_gres_stage(d_data, n, d, dir, k, plan, ws, d_sky_idx, d_step_idx, d_tests, st, bits);

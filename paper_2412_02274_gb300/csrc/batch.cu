@@ -70,7 +70,7 @@ gres_status normalize_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *o
     if (cfg) c = *cfg; else c.scheme = GRES_PART_GRID;
     if (c.scheme < GRES_PART_NONE || c.scheme > GRES_PART_SLICED) return fail(GRES_EINVAL, "cfg.scheme must be a gres_part");
     if (c.reserved != 0) return fail(GRES_EINVAL, "cfg.reserved must be 0");
-    if (c.flags & ~GRES_FLAG_COUNT_TESTS) return fail(GRES_EINVAL, "unknown cfg.flags bits");
+    if (c.flags & ~GRES_FLAG_COUNT_TESTS) return fail(GRES_EINVAL, "cfg.flags: only GRES_FLAG_COUNT_TESTS here");
     if (c.reps == 0) c.reps = gres::kMaxReps;
     if (c.reps < 1 || c.reps > gres::kMaxReps) return fail(GRES_EINVAL, "cfg.reps must be in [1, 1024]");
     if (c.slots == 0) c.slots = 8;

@@ -78,7 +78,8 @@ struct Workspace {
     uint32_t *tmin;               // tiles * DP per-tile minima
     uint32_t *smin;               // super-tiles (1024 rows) * DP minima
     uint32_t *perm;               // n: partition position -> skyline position
-    int32_t *res;                 // n: result per partition position
+    int32_t *res;                 // n: per partition position, a bound on the result (GRES_FLAG_GRES_REPS)
+    uint32_t *greps;              // 32 * DP: the gres-stage representatives (GRES_FLAG_GRES_REPS)
     uint32_t *steps;              // K widths
     uint32_t *magic;              // K * 4 multiply-high constants (m, s1, s2, delta)
     size_t bytes;
@@ -211,6 +212,9 @@ struct DomQuery {
     // intervals g over values read as v / 2^B, projection floor(v g / 2^B)
     // (magic holds g's division constants, steps the pruning widths).
     int gbits = 0;
+    // Optional bound per partition position (GRES_FLAG_GRES_REPS): a step at
+    // which the target is known to leave; the search looks only below it.
+    const int32_t *ub = nullptr;
 };
 
 // Division constants to make on the device for one query (k_make_magic).
@@ -232,7 +236,7 @@ constexpr int64_t kClusterSortMax = 131072;
 cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
                               int max_passes, cudaStream_t st);
 cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,
-                           Workspace &ws, int64_t *d_sky_idx, cudaStream_t st);
+                           Workspace &ws, int64_t *d_sky_idx, cudaStream_t st, bool gres_reps = false);
 cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir, int k,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t *d_sky_idx, int32_t *d_step_idx,

@@ -630,6 +630,76 @@ __device__ __forceinline__ void cell_bounds(uint32_t x, uint32_t dm1, int dir, u
     hi = dir ? x : x + e;
 }
 
+// Raw cell [lv, uv] of raw value v at one step (mg = the step's division
+// constants and divisor). Widths: [floor(v / w) w, + w - 1] cut at 2^32 - 1.
+// Grid parameter g over v / 2^B: with v g = c 2^B + r, [v - floor(r / g),
+// v + floor((2^B - 1 - r) / g)] cut at 2^32 - 1.
+__device__ __forceinline__ void raw_cell(uint32_t v, uint4 mg, int gbits, uint32_t &lv, uint32_t &uv) {
+    if (gbits) {
+        const unsigned long long mask = (1ull << gbits) - 1ull;
+        const uint32_t r = (uint32_t)(((unsigned long long)v * mg.w) & mask);
+        lv = v - udiv(r, mg.x, mg.y, mg.z);
+        const unsigned long long u = (unsigned long long)v + udiv((uint32_t)(mask - r), mg.x, mg.y, mg.z);
+        uv = u > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)u;
+    } else {
+        const uint32_t delta = mg.w;
+        lv = udiv(v, mg.x, mg.y, mg.z) * delta;
+        uv = lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+    }
+}
+
+// Representative Filtering in the gres stage (GRES_FLAG_GRES_REPS): for the
+// target at partition position i, the first step at which one of the 32
+// representatives' projections dominates the target's (K if none), as a
+// bound for the search. One warp per target, lanes over 32 steps at a time.
+template <int D>
+__global__ void __launch_bounds__(256)
+k_rep_bound(const uint32_t *cand, const uint32_t *greps, const long long *n_sky, const uint32_t *magic,
+            int K, int dir, int gbits, int32_t *ub, unsigned long long *tests) {
+    constexpr int DP = padded_dims(D);
+    __shared__ uint32_t rs[32 * DP];
+    for (int j = threadIdx.x; j < 32 * DP; j += blockDim.x) rs[j] = greps[j];
+    __syncthreads();
+    const long long S = *n_sky;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long n_tests = 0;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < S; i += nw) {
+        uint32_t t[D];
+        ld_row<D>(cand, i, t);
+        int result = K;
+        for (int w0 = 0; w0 < K && result == K; w0 += 32) {
+            const int k = w0 + lane;
+            const bool live = k < K;
+            const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(magic) + k) : make_uint4(1u, 0u, 0u, 1u);
+            uint32_t lo[D], hi[D];
+            #pragma unroll
+            for (int q = 0; q < D; q++) {
+                uint32_t lv, uv;
+                raw_cell(dir ? ~t[q] : t[q], mg, gbits, lv, uv);
+                hi[q] = live ? (dir ? ~lv : uv) : 0u;
+                lo[q] = live ? (dir ? ~uv : lv) : 0u;
+            }
+            bool hit = false;
+            for (int r = 0; r < 32; r++) {
+                bool le = true, lt = false;
+                #pragma unroll
+                for (int q = 0; q < D; q++) {
+                    const uint32_t sv = rs[r * DP + q];
+                    le &= sv <= hi[q];
+                    lt |= sv < lo[q];
+                }
+                hit |= le & lt;
+            }
+            n_tests += 32 * 32;
+            const unsigned msk = __ballot_sync(kFull, hit);
+            if (msk) result = w0 + __ffs(msk) - 1;
+        }
+        if (lane == 0) ub[i] = result;
+    }
+    if (tests && lane == 0 && n_tests) atomicAdd(tests, n_tests);
+}
+
 // Grid resistance of the target at partition position i of query q (one
 // warp; every lane returns it): the first step at which some candidate's
 // projection dominates the target's projection, else K.
@@ -660,11 +730,16 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
         uint32_t X[SLOTS][D], Y[PK ? 1 : SLOTS][PK ? 1 : D], dm1[PK ? SLOTS : 1];
         unsigned ready = 0;   // slots whose bounds are made
         int best = wcount;
+        if (qy.ub) {
+            // a known exit step (GRES_FLAG_GRES_REPS): only earlier steps are searched
+            const int b = qy.ub[i];
+            if (b >= w0 && b - w0 < wcount) best = b - w0;
+        }
         // keys hold excesses >> qshift; only excesses below the window's widest width matter
         const uint32_t wmax = wsteps[wcount - 1];
         const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
         // wl: the width of step best - 1 (excesses at or above it cannot matter), wlq: its key
-        uint32_t wl = wmax, wlq = min(wmax >> qshift, 0x7FFFFFFu);
+        uint32_t wl = best > 0 ? wsteps[best - 1] : 0u, wlq = min(wl >> qshift, 0x7FFFFFFu);
         // lane j < SLOTS - 1 holds the widest width of slot j (for the first slot that can matter)
         const uint32_t slot_top = (lane < SLOTS - 1 && 32 * lane + 31 < wcount) ? wsteps[32 * lane + 31] : 0xFFFFFFFFu;
         // Best-first over three levels -- 1024-row super-tiles, 32-row tiles, rows --
@@ -770,27 +845,14 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                                 #pragma unroll
                                 for (int q = 0; q < D; q++) {
                                     const uint32_t v = qy.dir ? ~t[q] : t[q];
-                                    if (GM) {
-                                        // cell of floor(v g / 2^B): with v g = c 2^B + r it is
-                                        // [v - floor(r / g), v + floor((2^B - 1 - r) / g)]
-                                        const unsigned long long mask = (1ull << qy.gbits) - 1ull;
-                                        const uint32_t r = (uint32_t)(((unsigned long long)v * delta) & mask);
-                                        const uint32_t lv = v - udiv(r, mg.x, mg.y, mg.z);
-                                        const unsigned long long u =
-                                            (unsigned long long)v + udiv((uint32_t)(mask - r), mg.x, mg.y, mg.z);
-                                        const uint32_t uv = u > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)u;
-                                        X[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
-                                        Y[PK ? 0 : j][PK ? 0 : q] = live ? (qy.dir ? ~uv : lv) : 0u;
-                                        continue;
-                                    }
-                                    const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
                                     if (PK) {
                                         // raw cell [lv, lv + min(delta - 1, ~lv)]: canonical low corner lv
                                         // (MIN) or canonical high corner ~lv (MAX); lanes past K never match
+                                        const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
                                         X[j][q] = live ? (qy.dir ? ~lv : lv) : 0u;
                                     } else {
-                                        const uint32_t uv =
-                                            lv > 0xFFFFFFFFu - (delta - 1u) ? 0xFFFFFFFFu : lv + (delta - 1u);
+                                        uint32_t lv, uv;
+                                        raw_cell(v, mg, GM ? qy.gbits : 0, lv, uv);
                                         X[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
                                         Y[PK ? 0 : j][PK ? 0 : q] = live ? (qy.dir ? ~uv : lv) : 0u;
                                     }
@@ -1211,6 +1273,17 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
     q.K = k;
     q.dir = dir;
     q.gbits = gbits;
+    unsigned long long *counts = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;
+    if (cfg.flags & GRES_FLAG_GRES_REPS) {
+        q.ub = ws.res;
+        const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)g_sm_count * 8);
+#define GRES_RB(D) (k_rep_bound<D><<<blocks, 256, 0, st>>>(ws.cand, ws.greps, &ws.hdr->n_sky, ws.magic, k, dir, \
+                    gbits, ws.res, counts), note_launch(), cudaGetLastError())
+        auto rep_bound = [&]() -> cudaError_t { GRES_DISPATCH_D(d, GRES_RB) };
+#undef GRES_RB
+        e = rep_bound();
+        if (e != cudaSuccess) return e;
+    }
     stage_begin(kStageDominance, st);
     e = launch_dominance(d, cfg.slots, q, &ws.hdr->work_next,
                          (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr, st);

@@ -282,27 +282,12 @@ k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *his
 // representative stay: by transitivity the filter drops exactly the same
 // rows with or without them. Also clears the filter's per-segment survivor
 // counts (nb of them).
-template <int D>
-__global__ void __launch_bounds__(kMaxReps)
-k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, uint32_t *rows,
-           uint32_t *blocksum, long long nb) {
-    __shared__ unsigned long long sk[kMaxReps];
-    __shared__ uint32_t lo[D], hi[D];
+// Bitonic sort of one value per thread over a block of kMaxReps threads
+// (compare-exchange partners under 32 apart through warp shuffles, the others
+// through shared memory sk); returns this thread's value of the ascending
+// order.
+__device__ __forceinline__ unsigned long long block_bitonic(unsigned long long v, unsigned long long *sk) {
     const int tid = threadIdx.x;
-    for (long long j = tid; j < nb; j += kMaxReps) blocksum[j] = 0u;
-    const int nc = (int)min((long long)h->n_cand, (long long)kMaxReps);
-    if (tid < D) { lo[tid] = 0xFFFFFFFFu; hi[tid] = 0u; }
-    __syncthreads();
-    uint32_t x[D];
-    const uint32_t idx = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
-    if (tid < nc) {
-        load_canon<D>(data, idx, dir, x);
-        #pragma unroll
-        for (int q = 0; q < D; q++) { atomicMin(&lo[q], x[q]); atomicMax(&hi[q], x[q]); }
-    }
-    __syncthreads();
-    const int bits = min(16, 32 / D);
-    unsigned long long v = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 32) | idx : ~0ull;
     for (int size = 2; size <= kMaxReps; size <<= 1) {
         const bool asc = (tid & size) == 0;
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -320,6 +305,52 @@ k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, 
             v = (asc == lower) ? mn : mx;
         }
     }
+    return v;
+}
+
+// greps (may be NULL): also the 32 candidates of smallest f, canonical rows
+// padded with sentinel rows, for the gres stage's representatives.
+template <int D>
+__global__ void __launch_bounds__(kMaxReps)
+k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, uint32_t *rows,
+           uint32_t *blocksum, long long nb, uint32_t *greps) {
+    __shared__ unsigned long long sk[kMaxReps];
+    __shared__ uint32_t lo[D], hi[D];
+    const int tid = threadIdx.x;
+    for (long long j = tid; j < nb; j += kMaxReps) blocksum[j] = 0u;
+    const int nc = (int)min((long long)h->n_cand, (long long)kMaxReps);
+    if (tid < D) { lo[tid] = 0xFFFFFFFFu; hi[tid] = 0u; }
+    __syncthreads();
+    uint32_t x[D];
+    const uint32_t idx = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
+    if (tid < nc) {
+        load_canon<D>(data, idx, dir, x);
+        #pragma unroll
+        for (int q = 0; q < D; q++) { atomicMin(&lo[q], x[q]); atomicMax(&hi[q], x[q]); }
+    }
+    __syncthreads();
+    if (greps) {
+        // f < 2^35 and tid < 2^10: (f, candidate) in one 64-bit key
+        unsigned long long f = 0;
+        #pragma unroll
+        for (int q = 0; q < D; q++) f += tid < nc ? x[q] : 0u;
+        const unsigned long long g = block_bitonic(tid < nc ? (f << 10) | (unsigned long long)tid : ~0ull, sk);
+        __syncthreads();
+        if (tid < 32) {
+            constexpr int DP = padded_dims(D);
+            uint32_t y[D];
+            if (g != ~0ull) {
+                load_canon<D>(data, rep_idx[(int)(g & 1023ull)], dir, y);
+                store_row<D>(greps, tid, y);
+            } else {
+                #pragma unroll
+                for (int q = 0; q < DP; q++) greps[tid * DP + q] = kSentinel;
+            }
+        }
+    }
+    const int bits = min(16, 32 / D);
+    unsigned long long v = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 32) | idx : ~0ull;
+    v = block_bitonic(v, sk);
     if (tid < nc) {
         load_canon<D>(data, (uint32_t)(v & 0xFFFFFFFFull), dir, x);
         store_row<D>(rows, tid, x);
@@ -794,7 +825,7 @@ k_surv_cluster(Workspace ws) {
 
 template <int D>
 cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Workspace &ws,
-                      int64_t *d_sky_idx, cudaStream_t st) {
+                      int64_t *d_sky_idx, cudaStream_t st, bool gres_reps) {
     const long long nb = (n + kCB - 1) / kCB;
     const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 4);
     cudaError_t e = cudaMemsetAsync(ws.sel_hist, 0, sizeof(uint32_t) * 2 * kSelBuckets, st);
@@ -803,7 +834,8 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     k_keys<D><<<hb, 1024, 0, st>>>(d_data, n, dir, ws.keys[0], ws.hdr, ws.sel_hist, reps); note_launch();
     k_sel_l2<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, ws.sel_hist + kSelBuckets, reps, ws.keys[1],
                                   ws.rep_idx); note_launch();
-    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_idx, ws.hdr, ws.reps, ws.blocksum, nb); note_launch();
+    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_idx, ws.hdr, ws.reps, ws.blocksum, nb,
+                                          gres_reps ? ws.greps : nullptr); note_launch();
     static int filter_blocks = 0;   // resident blocks of k_filter<D> on this GPU
     if (filter_blocks == 0) {
         int per_sm = 0, dev = 0, sms = 0;
@@ -850,17 +882,17 @@ cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st) {
 }
 
 cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,
-                           Workspace &ws, int64_t *d_sky_idx, cudaStream_t st) {
+                           Workspace &ws, int64_t *d_sky_idx, cudaStream_t st, bool gres_reps) {
     if (n == 0) return cudaSuccess;
     switch (d) {
-        case 1: return skyline_d<1>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 2: return skyline_d<2>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 3: return skyline_d<3>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 4: return skyline_d<4>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 5: return skyline_d<5>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 6: return skyline_d<6>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 7: return skyline_d<7>(d_data, n, dir, reps, ws, d_sky_idx, st);
-        case 8: return skyline_d<8>(d_data, n, dir, reps, ws, d_sky_idx, st);
+        case 1: return skyline_d<1>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 2: return skyline_d<2>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 3: return skyline_d<3>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 4: return skyline_d<4>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 5: return skyline_d<5>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 6: return skyline_d<6>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 7: return skyline_d<7>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
+        case 8: return skyline_d<8>(d_data, n, dir, reps, ws, d_sky_idx, st, gres_reps);
         default: return cudaErrorInvalidValue;
     }
 }

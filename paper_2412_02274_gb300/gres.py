@@ -20,6 +20,7 @@ from . import build as _build
 MIN, MAX = 0, 1
 PART_NONE, PART_GRID, PART_ANGULAR, PART_SLICED = 0, 1, 2, 3
 FLAG_COUNT_TESTS = 1
+FLAG_GRES_REPS = 2
 
 _STATUS = {0: "GRES_OK", 1: "GRES_EINVAL", 2: "GRES_ENOMEM", 3: "GRES_EAGAIN",
            4: "GRES_ETIMEOUT", 5: "GRES_ECUDA", 6: "GRES_EINTERNAL"}
@@ -60,8 +61,9 @@ class Instance(ctypes.Structure):
 
 
 def plan(scheme: int = PART_GRID, m: int = 0, p: int = 0, slice_dim: int = 0, reps: int = 0,
-         slots: int = 0, count_tests: bool = False) -> PlanCfg:
-    return PlanCfg(scheme, m, p, slice_dim, reps, slots, FLAG_COUNT_TESTS if count_tests else 0, 0)
+         slots: int = 0, count_tests: bool = False, gres_reps: bool = False) -> PlanCfg:
+    flags = (FLAG_COUNT_TESTS if count_tests else 0) | (FLAG_GRES_REPS if gres_reps else 0)
+    return PlanCfg(scheme, m, p, slice_dim, reps, slots, flags, 0)
 
 
 def library_path() -> str:

@@ -144,3 +144,20 @@ def test_gmode_argument_checks_need_no_gpu():
         rc = lib.gres_compute_g(fake, 10, 2, 0, bits, g.ctypes.data_as(ctypes.c_void_p), len(g), None,
                                 fake, 1 << 30, fake, fake, None, ctypes.byref(cnt), None, None)
         assert rc == 1, (bits, gl)
+
+
+def test_gres_reps_flag_rejected_where_not_supported():
+    lib = G.load()
+    out = ctypes.c_void_p()
+    cfg = G.plan(G.PART_GRID, gres_reps=True)
+    data = np.zeros((4, 2), np.uint32)
+    rc = lib.gres_dataset_create(data.ctypes.data_as(ctypes.c_void_p), 4, 2, 0, ctypes.byref(cfg), 1, None,
+                                 ctypes.byref(out))
+    assert rc == 1 and b"flags" in lib.gres_last_error()
+    bad = G.PlanCfg(G.PART_GRID, 0, 0, 0, 0, 0, 4, 0)   # an unknown flag bit
+    fake = ctypes.c_void_p(256)
+    steps = np.array([1, 2], np.uint32)
+    cnt = ctypes.c_int64(0)
+    rc = lib.gres_compute(fake, 10, 2, 0, steps.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(bad),
+                          fake, 1 << 30, fake, fake, None, ctypes.byref(cnt), None, None)
+    assert rc == 1
