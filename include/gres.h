@@ -98,8 +98,8 @@ typedef struct {
  * tuple is tested at every step against the 32 rows of smallest f (sum of the
  * values; by stability any rows of r may serve as candidates), and the first
  * step at which one of them dominates bounds the search. Results are
- * unchanged. Honoured by gres_compute and gres_compute_g (rejected by the
- * dataset, batch and server calls). With GRES_FLAG_COUNT_TESTS the
+ * unchanged. Honoured by gres_compute, gres_compute_g and gres_batch
+ * (rejected by the dataset and server calls). With GRES_FLAG_COUNT_TESTS the
  * representative tests are counted in d_tests[0] too. */
 #define GRES_FLAG_GRES_REPS 2
 

@@ -30,9 +30,10 @@ class Candidate:
     m: int = 0
     p: int = 0
     slots: int = 8
+    gres_reps: bool = False
 
     def cfg(self) -> G.PlanCfg:
-        return G.plan(self.scheme, m=self.m, p=self.p, slots=self.slots)
+        return G.plan(self.scheme, m=self.m, p=self.p, slots=self.slots, gres_reps=self.gres_reps)
 
 
 def default_candidates() -> list[Candidate]:
@@ -44,6 +45,9 @@ def default_candidates() -> list[Candidate]:
                 Candidate(f"angular-auto-s{slots}", G.PART_ANGULAR, slots=slots),
                 Candidate(f"sliced-p64-s{slots}", G.PART_SLICED, p=64, slots=slots),
                 Candidate(f"none-s{slots}", G.PART_NONE, slots=slots)]
+    # Representative Filtering in the gres stage on the usual winners
+    out += [Candidate(f"{c.name}-reps", c.scheme, c.m, c.p, c.slots, True)
+            for c in out if c.name.startswith(("grid-auto", "grid-m2", "grid-m3", "none"))]
     return out
 
 

@@ -63,14 +63,15 @@ gres_status check_common(int64_t n, int32_t d, int32_t dir) {
     return GRES_OK;
 }
 
-gres_status normalize_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *out) {
+gres_status normalize_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *out, bool allow_reps = false) {
     // the same defaults and limits as gres_compute
     gres_plan_cfg c;
     std::memset(&c, 0, sizeof(c));
     if (cfg) c = *cfg; else c.scheme = GRES_PART_GRID;
     if (c.scheme < GRES_PART_NONE || c.scheme > GRES_PART_SLICED) return fail(GRES_EINVAL, "cfg.scheme must be a gres_part");
     if (c.reserved != 0) return fail(GRES_EINVAL, "cfg.reserved must be 0");
-    if (c.flags & ~GRES_FLAG_COUNT_TESTS) return fail(GRES_EINVAL, "cfg.flags: only GRES_FLAG_COUNT_TESTS here");
+    const int allowed = GRES_FLAG_COUNT_TESTS | (allow_reps ? GRES_FLAG_GRES_REPS : 0);
+    if (c.flags & ~allowed) return fail(GRES_EINVAL, "cfg.flags: flag not supported by this call");
     if (c.reps == 0) c.reps = gres::kMaxReps;
     if (c.reps < 1 || c.reps > gres::kMaxReps) return fail(GRES_EINVAL, "cfg.reps must be in [1, 1024]");
     if (c.slots == 0) c.slots = 8;
@@ -321,7 +322,7 @@ gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, si
     std::vector<gres_plan_cfg> plans((size_t)n_inst);
     for (int32_t i = 0; i < n_inst; i++) {
         const gres_instance &x = inst[i];
-        if ((s = normalize_plan(&x.cfg, x.d, &plans[(size_t)i])) != GRES_OK) return s;
+        if ((s = normalize_plan(&x.cfg, x.d, &plans[(size_t)i], true)) != GRES_OK) return s;
         if (x.n > 0 && (!x.d_data || !x.d_steps || !x.d_sky_idx || !x.d_step_idx))
             return fail(GRES_EINVAL, "instance " + std::to_string(i) + ": NULL buffer");
     }
@@ -353,8 +354,11 @@ gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, si
         cudaStream_t si = pool->s[i % kPoolStreams];
         gres::Workspace &w = ws[(size_t)i];
         e = gres::launch_init(w, x.n, si);
-        if (e == cudaSuccess) e = gres::launch_skyline(x.d_data, x.n, x.d, x.dir, plans[(size_t)i].reps, w, x.d_sky_idx, si);
+        const bool greps = (plans[(size_t)i].flags & GRES_FLAG_GRES_REPS) != 0;
+        if (e == cudaSuccess)
+            e = gres::launch_skyline(x.d_data, x.n, x.d, x.dir, plans[(size_t)i].reps, w, x.d_sky_idx, si, greps);
         if (e == cudaSuccess) e = gres::launch_partition(x.d, plans[(size_t)i], x.n, w, si);
+        if (e == cudaSuccess && greps) e = gres::launch_rep_bound(x.d, x.n, w, x.k, x.dir, 0, nullptr, si);
         if (e == cudaSuccess && x.d_sky_count)
             e = cudaMemcpyAsync(x.d_sky_count, &w.hdr->n_sky, sizeof(int64_t), cudaMemcpyDeviceToDevice, si);
         if (e != cudaSuccess) return cuda_fail(e, "batch skyline");
@@ -382,6 +386,7 @@ gres_status gres_batch(const gres_instance *inst, int32_t n_inst, void *d_ws, si
                 q.out = x.d_step_idx;
                 q.K = x.k;
                 q.dir = x.dir;
+                if (plans[(size_t)i].flags & GRES_FLAG_GRES_REPS) q.ub = ws[(size_t)i].res;
                 qs.push_back(q);
             }
             for (size_t off = 0; off < qs.size(); off += 256) {

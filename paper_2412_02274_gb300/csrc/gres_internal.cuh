@@ -241,6 +241,10 @@ cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t *d_sky_idx, int32_t *d_step_idx,
                               unsigned long long *d_tests, cudaStream_t st, int gbits = 0);
+// Per target, the first step at which one of the 32 gres-stage representatives
+// (ws.greps) dominates, into ws.res (GRES_FLAG_GRES_REPS); after the partitioning.
+cudaError_t launch_rep_bound(int d, int64_t n, Workspace &ws, int k, int dir, int gbits,
+                             unsigned long long *tests, cudaStream_t st);
 // The candidate partitioning of the skyline in ws (cand, tmin, perm).
 cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st);
 // The caller's rows as the candidate set (canonical padded rows into

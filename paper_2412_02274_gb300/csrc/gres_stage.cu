@@ -1252,6 +1252,18 @@ cudaError_t launch_make_magic(const MagicJob *jobs, int count, cudaStream_t st) 
     return cudaGetLastError();
 }
 
+cudaError_t launch_rep_bound(int d, int64_t n, Workspace &ws, int k, int dir, int gbits,
+                             unsigned long long *tests, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = device_props();
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)g_sm_count * 8);
+#define GRES_RB(D) (k_rep_bound<D><<<blocks, 256, 0, st>>>(ws.cand, ws.greps, &ws.hdr->n_sky, ws.magic, k, dir, \
+                    gbits, ws.res, tests), note_launch(), cudaGetLastError())
+    GRES_DISPATCH_D(d, GRES_RB)
+#undef GRES_RB
+}
+
 cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int dir, int k,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t * /*d_sky_idx*/, int32_t *d_step_idx,
@@ -1274,17 +1286,15 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
     q.dir = dir;
     q.gbits = gbits;
     unsigned long long *counts = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;
+    stage_begin(kStageDominance, st);   // the representative bound pass counts as grid-dominance work
     if (cfg.flags & GRES_FLAG_GRES_REPS) {
         q.ub = ws.res;
-        const int blocks = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)g_sm_count * 8);
-#define GRES_RB(D) (k_rep_bound<D><<<blocks, 256, 0, st>>>(ws.cand, ws.greps, &ws.hdr->n_sky, ws.magic, k, dir, \
-                    gbits, ws.res, counts), note_launch(), cudaGetLastError())
-        auto rep_bound = [&]() -> cudaError_t { GRES_DISPATCH_D(d, GRES_RB) };
-#undef GRES_RB
-        e = rep_bound();
-        if (e != cudaSuccess) return e;
+        e = launch_rep_bound(d, n, ws, k, dir, gbits, counts, st);
+        if (e != cudaSuccess) {
+            stage_end(kStageDominance, st);
+            return e;
+        }
     }
-    stage_begin(kStageDominance, st);
     e = launch_dominance(d, cfg.slots, q, &ws.hdr->work_next,
                          (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr, st);
     stage_end(kStageDominance, st);

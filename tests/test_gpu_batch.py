@@ -69,7 +69,7 @@ def _problems(count, seed):
         steps = steps_log(k, 16)
         direction = G.MIN if i % 4 else G.MAX
         cfg = G.plan([G.PART_GRID, G.PART_ANGULAR, G.PART_SLICED, G.PART_NONE][i % 4],
-                     slots=4 if i % 5 == 0 else 8)
+                     slots=4 if i % 5 == 0 else 8, gres_reps=i % 3 == 1)
         probs.append({"data": G.to_device_u32(data),
                       "steps": torch.from_numpy(steps.view(np.int32)).cuda(),
                       "direction": direction, "cfg": cfg})
