@@ -252,6 +252,8 @@ __device__ __forceinline__ void cluster_radix_sort(cg::cluster_group &cl, uint32
 constexpr int kClSmemCap = 8192;
 // dynamic shared memory: the sort's words plus two (key, value) buffers
 constexpr size_t kClSmemBytes = kClSortBytes + sizeof(uint32_t) * 4 * (size_t)kClSmemCap;
+static_assert((int64_t)kClCTAs * kClSmemCap >= kClusterSortMax,
+              "the shared-memory sort must hold every input the cluster path takes");
 
 __device__ __forceinline__ long long cluster_chunk(long long n) {
     return (((n + kClCTAs - 1) / kClCTAs) + 31) & ~31LL;
