@@ -155,12 +155,18 @@ gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t d
                          unsigned long long *d_tests, void *stream);
 
 /* Host-buffer form of gres_compute: copies h_data to the device, computes,
- * and copies the S results back, all on `stream`, then waits for it.
+ * and copies the S results back, then waits; later work on `stream` is
+ * ordered after it.
  *   h_data       host, n*d uint32 row-major (pinned memory copies faster)
  *   d_ws         device scratch, >= gres_workspace_size_host(n, d, k) bytes
  *   h_sky_idx    host, capacity n int64
  *   h_step_idx   host, capacity n int32
- *   h_sky_count  host int64 (required) */
+ *   h_sky_count  host int64 (required)
+ * With pinned h_data the calling thread keeps up to 4 captured CUDA graphs,
+ * keyed by (h_data, n, d, dir, widths, plan, d_ws, device). A call matching
+ * one replays it on a library stream: one graph launch instead of a dozen
+ * kernel launches. The replay reads h_data's current contents. Kernels
+ * replayed this way are counted once by gres_launch_count, at capture. */
 gres_status gres_workspace_size_host(int64_t n, int32_t d, int32_t k, size_t *bytes);
 gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int32_t dir,
                               const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,

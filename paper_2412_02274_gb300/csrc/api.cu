@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 namespace {
@@ -259,7 +260,7 @@ gres_status gres_workspace_size_host(int64_t n, int32_t d, int32_t k, size_t *by
     gres_status s = gres_workspace_size(n, d, k, bytes);
     if (s != GRES_OK) return s;
     const int64_t nn = n > 0 ? n : 1;
-    *bytes += align256(4 * (size_t)nn * d) + align256(8 * (size_t)nn) + align256(4 * (size_t)nn);
+    *bytes += align256(4 * (size_t)nn * d) + align256(8 * (size_t)nn) + align256(4 * (size_t)nn) + 256;
     return GRES_OK;
 }
 
@@ -355,6 +356,43 @@ gres_status gres_compute_g(const uint32_t *d_data, int64_t n, int32_t d, int32_t
     return finish_counts(ws, d_sky_count, h_sky_count, st);
 }
 
+namespace {
+
+// gres_compute_host keeps one CUDA graph per (input buffer, shape, widths,
+// plan, workspace, device) for pinned inputs: the input copy, the whole
+// computation and the copy of S and the status word back. A repeated call
+// with the same arguments replays it -- one graph launch instead of a dozen
+// kernel launches -- and then copies the S results. The first call of a key
+// runs directly (which also sets every kernel's launch attributes outside any
+// capture) and captures the graph afterwards without running it.
+struct HostGraph {
+    const uint32_t *h_data = nullptr;
+    int64_t n = 0;
+    int32_t d = 0, dir = 0;
+    std::vector<uint32_t> steps;
+    gres_plan_cfg cfg;
+    void *d_ws = nullptr;
+    int device = -1;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    int64_t *h_out = nullptr;     // pinned: [0] S, [1] the header's status word (low 32 bits)
+    unsigned long long used = 0;
+};
+constexpr size_t kHostGraphs = 4;
+thread_local std::vector<HostGraph> g_host_graphs;
+thread_local unsigned long long g_host_clock = 0;
+
+void host_graph_free(HostGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.ev) cudaEventDestroy(g.ev);
+    if (g.st) cudaStreamDestroy(g.st);
+    if (g.h_out) cudaFreeHost(g.h_out);
+    g = HostGraph();
+}
+
+}  // namespace
+
 gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int32_t dir,
                               const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,
                               void *d_ws, size_t ws_bytes,
@@ -375,14 +413,89 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
     uint32_t *d_data = reinterpret_cast<uint32_t *>(extra);
     int64_t *d_sky = reinterpret_cast<int64_t *>(extra + align256(4 * (size_t)nn * d));
     int32_t *d_res = reinterpret_cast<int32_t *>(extra + align256(4 * (size_t)nn * d) + align256(8 * (size_t)nn));
+    int64_t *d_count = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(d_res) + align256(4 * (size_t)nn));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (n > 0) {
-        cudaError_t e = cudaMemcpyAsync(d_data, h_data, 4 * (size_t)n * d, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    cudaError_t e;
+    gres_plan_cfg plan_key;
+    std::memset(&plan_key, 0, sizeof(plan_key));
+    if (cfg) plan_key = *cfg;
+    int device = 0;
+    if ((e = cudaGetDevice(&device)) != cudaSuccess) return cuda_fail(e, "device");
+    cudaPointerAttributes pa;
+    const bool pinned = n > 0 && cudaPointerGetAttributes(&pa, h_data) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();   // clear a lookup error on unregistered memory
+    HostGraph *hit = nullptr;
+    if (pinned && k >= 1 && h_steps) {
+        for (HostGraph &g : g_host_graphs)
+            if (g.exec && g.h_data == h_data && g.n == n && g.d == d && g.dir == dir && g.d_ws == d_ws &&
+                g.device == device && std::memcmp(&g.cfg, &plan_key, sizeof(plan_key)) == 0 &&
+                g.steps.size() == (size_t)k && std::memcmp(g.steps.data(), h_steps, 4 * (size_t)k) == 0)
+                hit = &g;
     }
     int64_t S = 0;
-    s = gres_compute(d_data, n, d, dir, h_steps, k, cfg, d_ws, core, d_sky, d_res, nullptr, &S, nullptr, stream);
-    if (s != GRES_OK) return s;
+    if (hit) {
+        hit->used = ++g_host_clock;
+        if ((e = cudaEventRecord(hit->ev, st)) != cudaSuccess) return cuda_fail(e, "host graph");
+        if ((e = cudaStreamWaitEvent(hit->st, hit->ev, 0)) != cudaSuccess) return cuda_fail(e, "host graph");
+        if ((e = cudaGraphLaunch(hit->exec, hit->st)) != cudaSuccess) return cuda_fail(e, "host graph");
+        if ((e = cudaStreamSynchronize(hit->st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+        const unsigned status = (unsigned)hit->h_out[1];
+        if (status & gres::kStatusTimeout) return fail(GRES_ETIMEOUT, "a bounded device wait ran out");
+        if (status & gres::kStatusInternal) return fail(GRES_EINTERNAL, "internal device check failed");
+        S = hit->h_out[0];
+        st = hit->st;
+    } else {
+        if (n > 0) {
+            e = cudaMemcpyAsync(d_data, h_data, 4 * (size_t)n * d, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "input copy");
+        }
+        s = gres_compute(d_data, n, d, dir, h_steps, k, cfg, d_ws, core, d_sky, d_res, nullptr, &S, nullptr, stream);
+        if (s != GRES_OK) return s;
+        if (pinned) {
+            // capture the same work for the next call with these arguments
+            HostGraph g;
+            g.h_data = h_data;
+            g.n = n;
+            g.d = d;
+            g.dir = dir;
+            g.steps.assign(h_steps, h_steps + k);
+            g.cfg = plan_key;
+            g.d_ws = d_ws;
+            g.device = device;
+            bool ok = cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaMallocHost(&g.h_out, 2 * sizeof(int64_t)) == cudaSuccess;
+            cudaGraph_t graph = nullptr;
+            if (ok) ok = cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                bool body = cudaMemcpyAsync(d_data, h_data, 4 * (size_t)n * d, cudaMemcpyHostToDevice, g.st) ==
+                            cudaSuccess;
+                if (body) body = gres_compute(d_data, n, d, dir, h_steps, k, cfg, d_ws, core, d_sky, d_res, d_count,
+                                              nullptr, nullptr, g.st) == GRES_OK;
+                if (body) body = cudaMemcpyAsync(g.h_out, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                                 g.st) == cudaSuccess;
+                if (body) body = cudaMemcpyAsync(g.h_out + 1, &reinterpret_cast<gres::WsHeader *>(d_ws)->status,
+                                                 sizeof(unsigned), cudaMemcpyDeviceToHost, g.st) == cudaSuccess;
+                ok = cudaStreamEndCapture(g.st, &graph) == cudaSuccess && body;
+            }
+            if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (ok) {
+                g.h_out[1] = 0;
+                g.used = ++g_host_clock;
+                if (g_host_graphs.size() >= kHostGraphs) {
+                    auto old = std::min_element(g_host_graphs.begin(), g_host_graphs.end(),
+                                                [](const HostGraph &a, const HostGraph &b) { return a.used < b.used; });
+                    host_graph_free(*old);
+                    g_host_graphs.erase(old);
+                }
+                g_host_graphs.push_back(std::move(g));
+            } else {
+                host_graph_free(g);
+            }
+        }
+    }
     if (S > 0) {
         cudaError_t e = cudaMemcpyAsync(h_sky_idx, d_sky, 8 * (size_t)S, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "result copy");
@@ -390,6 +503,11 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
         if (e != cudaSuccess) return cuda_fail(e, "result copy");
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    }
+    if (hit) {
+        // later work on the caller's stream comes after the graph's
+        cudaEventRecord(hit->ev, hit->st);
+        cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), hit->ev, 0);
     }
     *h_sky_count = S;
     return GRES_OK;
