@@ -197,7 +197,6 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.surv_orig = static_cast<uint32_t *>(take(4 * nn));
     w.reps = static_cast<uint32_t *>(take(4 * DP * kMaxReps));
     w.sel_hist = static_cast<uint32_t *>(take(4 * 2 * 4096));
-    w.rep_key = static_cast<unsigned long long *>(take(8 * kMaxReps));
     w.rep_idx = static_cast<uint32_t *>(take(4 * kMaxReps));
     w.sky_rows = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.cand = static_cast<uint32_t *>(take(4 * DP * rows_pad));

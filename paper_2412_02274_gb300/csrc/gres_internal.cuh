@@ -36,7 +36,6 @@ struct WsHeader {
     long long n_sky;              // skyline size S
     long long n_reps;             // representatives kept (mutually non-dominated)
     long long n_cand;             // representative candidates (smallest keys)
-    unsigned long long sel_thr;   // level-2 selection threshold (sub-bucket)
     unsigned int sel_b1;          // level-1 selection bucket
     unsigned int sel_below;       // rows under bucket sel_b1
     unsigned int work_next;       // dynamic work counter of the gres kernel
@@ -71,7 +70,6 @@ struct Workspace {
     uint32_t *surv_orig;          // n original row numbers, sum order
     uint32_t *reps;               // kMaxReps * DP
     uint32_t *sel_hist;           // 2 * 4096 selection histogram counters
-    unsigned long long *rep_key;  // kMaxReps representative candidate keys
     uint32_t *rep_idx;            // kMaxReps representative candidate rows
     uint32_t *sky_rows;           // (n + tile) * DP canonical rows, skyline order
     uint32_t *cand;               // (n + tile) * DP canonical rows, partition order

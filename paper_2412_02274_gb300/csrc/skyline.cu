@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kMaxReps)
 k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, uint32_t *rows,
            uint32_t *blocksum, long long nb, uint32_t *greps) {
     __shared__ unsigned long long sk[kMaxReps];
+    __shared__ uint32_t xs[D * kMaxReps];   // the candidates' canonical rows, attribute-major
     __shared__ uint32_t lo[D], hi[D];
     const int tid = threadIdx.x;
     for (long long j = tid; j < nb; j += kMaxReps) blocksum[j] = 0u;
@@ -323,10 +324,17 @@ k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, 
     __syncthreads();
     uint32_t x[D];
     const uint32_t idx = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
-    if (tid < nc) {
-        load_canon<D>(data, idx, dir, x);
+    if (tid < nc) load_canon<D>(data, idx, dir, x);
+    #pragma unroll
+    for (int q = 0; q < D; q++) {
+        xs[q * kMaxReps + tid] = tid < nc ? x[q] : 0u;
+        uint32_t a = tid < nc ? x[q] : 0xFFFFFFFFu, b = tid < nc ? x[q] : 0u;
         #pragma unroll
-        for (int q = 0; q < D; q++) { atomicMin(&lo[q], x[q]); atomicMax(&hi[q], x[q]); }
+        for (int o = 16; o > 0; o >>= 1) {
+            a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if ((tid & 31) == 0 && a <= b) { atomicMin(&lo[q], a); atomicMax(&hi[q], b); }
     }
     __syncthreads();
     if (greps) {
@@ -340,7 +348,9 @@ k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, 
             constexpr int DP = padded_dims(D);
             uint32_t y[D];
             if (g != ~0ull) {
-                load_canon<D>(data, rep_idx[(int)(g & 1023ull)], dir, y);
+                const int c = (int)(g & 1023ull);
+                #pragma unroll
+                for (int q = 0; q < D; q++) y[q] = xs[q * kMaxReps + c];
                 store_row<D>(greps, tid, y);
             } else {
                 #pragma unroll
@@ -348,11 +358,17 @@ k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, 
             }
         }
     }
-    const int bits = min(16, 32 / D);
-    unsigned long long v = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 32) | idx : ~0ull;
+    // sort key: Morton code (22 / D bits per attribute) | row (31 bits) | slot
+    // (10 bits): ordered by code then row, and the slot finds the shared copy
+    const int bits = 22 / D;
+    unsigned long long v = tid < nc ? ((unsigned long long)morton<D>(x, lo, hi, bits) << 41) |
+                                          ((unsigned long long)idx << 10) | (unsigned long long)tid
+                                    : ~0ull;
     v = block_bitonic(v, sk);
     if (tid < nc) {
-        load_canon<D>(data, (uint32_t)(v & 0xFFFFFFFFull), dir, x);
+        const int c = (int)(v & 1023ull);
+        #pragma unroll
+        for (int q = 0; q < D; q++) x[q] = xs[q * kMaxReps + c];
         store_row<D>(rows, tid, x);
     }
     if (tid == 0) {
