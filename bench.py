@@ -666,7 +666,7 @@ def run_serve(args):
     from paper_2412_02274_gb300 import gres as G
     rng = np.random.default_rng(2)
     datas = serve_datasets()
-    sv = G.Server(64 << 30, max_batch=128, max_inflight=3)
+    sv = G.Server(64 << 30, max_batch=128, max_inflight=3, chunk_targets=args.chunk_targets)
     ids = [sv.add_dataset(x, G.MIN, G.plan(G.PART_GRID)) for x in datas]
     nq = 10000
     qs = [(ids[int(rng.integers(0, len(ids)))], steps_log(int(rng.integers(64, 257)), 16)) for _ in range(nq)]
@@ -723,7 +723,8 @@ def run_serve(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": "serve-10k", "datasets": len(datas), "n_range": [1000, 2000000],
-                       "d_range": [2, 8], "widths": [64, 256], "max_batch": 128, "max_inflight": 3},
+                       "d_range": [2, 8], "widths": [64, 256], "max_batch": 128, "max_inflight": 3,
+                       "chunk_targets": args.chunk_targets or 16384},
             "saturation": {"qps": sat_qps, "p50_ms": float(np.percentile(lats, 50)) / 1e6,
                            "p99_ms": float(np.percentile(lats, 99)) / 1e6},
             "poisson_80pct": {"lambda_qps": lam, "achieved_qps": nq / load_s,
@@ -749,6 +750,8 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=2048)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--tune-table", default="", help="batch-512: write the autotuned plan table (JSON) here")
+    ap.add_argument("--chunk-targets", type=int, default=0,
+                    help="serve-10k: targets per query piece (0: the library default)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -253,7 +253,7 @@ typedef struct {
     int32_t max_k;           /* longest step list accepted (0: 4096)                */
     int32_t start_paused;    /* nonzero: queue queries but start no batch until
                                 gres_serve_resume (admission control, tests)        */
-    int32_t chunk_targets;   /* targets per piece of a query (0: 65536; < 0: whole
+    int32_t chunk_targets;   /* targets per piece of a query (0: 16384; < 0: whole
                                 queries, no pieces)                                 */
 } gres_serve_cfg;
 

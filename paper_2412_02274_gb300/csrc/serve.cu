@@ -349,7 +349,7 @@ gres_status gres_serve_create(size_t hbm_budget_bytes, const gres_serve_cfg *cfg
     if (c.max_inflight == 0) c.max_inflight = 2;
     if (c.queue_capacity == 0) c.queue_capacity = 1 << 16;
     if (c.max_k == 0) c.max_k = 4096;
-    if (c.chunk_targets == 0) c.chunk_targets = 65536;
+    if (c.chunk_targets == 0) c.chunk_targets = 16384;
     if (c.max_batch < 1 || c.max_batch > 256) return fail(GRES_EINVAL, "max_batch must be in [1, 256]");
     if (c.max_inflight < 1 || c.max_inflight > 16) return fail(GRES_EINVAL, "max_inflight must be in [1, 16]");
     if (c.queue_capacity < 1) return fail(GRES_EINVAL, "queue_capacity must be >= 1");
