@@ -514,8 +514,17 @@ k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, uint
     if (clear && threadIdx.x == 0) blocksum[blockIdx.x] = 0u;   // k_final counts skyline rows here
 }
 
-// Sort keys of the survivors: a 16-bit Morton code over their range. Also
-// clears the skyline flags.
+// Bits per attribute of the survivors' Morton code when more than
+// kClusterSortMax rows survive: at least 4, so that at d >= 5 the final
+// check's tiles stay tight when many survivors are not skyline rows. Fewer
+// survivors keep 16 / D bits (a 16-bit code): there an extra digit pass costs
+// more than it saves.
+constexpr int surv_fine_bits(int D) { return 16 / D > 4 ? 16 / D : 4; }
+constexpr int surv_sort_passes(int D) { return (D * surv_fine_bits(D) + 7) / 8; }
+
+// Sort keys of the survivors: a Morton code over their range (see
+// surv_fine_bits). The radix sort runs only the digit passes that the key
+// range needs. Also clears the skyline flags.
 template <int D>
 __global__ void k_surv_keys(const uint32_t *surv_rows, WsHeader *h, unsigned long long *keys, uint32_t *vals,
                             uint32_t *skyflag, long long n) {
@@ -523,7 +532,7 @@ __global__ void k_surv_keys(const uint32_t *surv_rows, WsHeader *h, unsigned lon
          i += (long long)gridDim.x * blockDim.x)
         skyflag[i] = 0u;   // cleared for k_final
     const long long M = h->n_surv;
-    const int bits = 16 / D;
+    const int bits = M > kClusterSortMax ? surv_fine_bits(D) : 16 / D;
     const long long lim = ((M + 31) / 32) * 32;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < lim;
          r += (long long)gridDim.x * blockDim.x) {
@@ -872,7 +881,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
         if (e != cudaSuccess) return e;
     } else {
         k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
-        e = launch_radix_sort(ws, n, &ws.hdr->n_surv, 2, st);
+        e = launch_radix_sort(ws, n, &ws.hdr->n_surv, surv_sort_passes(D), st);
         if (e != cudaSuccess) return e;
         const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
         k_gather_tiles<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1],

@@ -145,6 +145,21 @@ def test_large_skyline_streams_from_global_memory(n):
     np.testing.assert_array_equal(gr[targets], exp)
 
 
+@pytest.mark.parametrize("d,n_plane,n_dom", [(5, 150000, 100000), (6, 200000, 150000), (8, 120000, 100000)])
+def test_large_path_many_survivors(d, n_plane, n_dom):
+    """More than 131,072 filter survivors on the multi-kernel path (finer survivor keys, up to
+    four digit passes): the planted skyline exactly, and gres of sampled skyline tuples
+    against the oracle over the whole skyline."""
+    from planted import planted_skyline
+    data, sky = planted_skyline(n_plane, n_dom, d, seed=d)
+    steps = steps_log(32, 16)
+    gs, gr = _gpu(data, steps, G.MIN, G.plan(G.PART_GRID))
+    np.testing.assert_array_equal(gs, sky)
+    pick = np.linspace(0, len(sky) - 1, 61).astype(np.int64)
+    exp = O.gres(data, steps, candidates=sky, targets=sky[pick], threads=THREADS)
+    np.testing.assert_array_equal(gr[pick], exp)
+
+
 def test_gproj_exhaustive_20bit():
     """gproj with multiply-high division equals floor division for every v < 2^20."""
     v = np.arange(1 << 20, dtype=np.uint32)

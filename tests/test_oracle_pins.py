@@ -213,6 +213,17 @@ def test_skyline_2d_staircase_and_1d():
     assert list(O.skyline_bnl(data)) == [1, 3]
 
 
+def test_planted_skyline_construction():
+    """The planted construction (plane rows plus dominated offsets) has the plane rows as its
+    skyline: checked against both oracle skylines, so the large GPU tests that rely on it
+    rest on a pinned expectation."""
+    from planted import planted_skyline
+    for d, seed in ((2, 0), (5, 1), (8, 2)):
+        data, sky = planted_skyline(1500, 1200, d, seed=seed)
+        assert list(O.skyline_bnl(data)) == list(sky)
+        assert list(O.skyline_allpairs(data)) == list(sky)
+
+
 def _expected_maxima(n, d):
     a = np.ones(n + 1)
     a[0] = 0.0
