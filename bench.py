@@ -235,6 +235,23 @@ def whole_job(total_ms: float, units: float, device):
     return t, u, (u / (t / 1e3) if t > 0 else 0.0)
 
 
+def measure_test_peak(G, torch, d: int, dev, stream, iters: int = 4096, reps: int = 5) -> dict:
+    """Measured peak of the dominance test on this GPU: the library's probe kernel (every
+    thread tests 16 register-held candidates per iteration, 2d compare lane-ops each), one
+    full wave of blocks, timed with CUDA events on `stream`; median of `reps` launches."""
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    G.test_peak_probe(d, iters, sink, stream=stream)
+    rates = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ops = G.test_peak_probe(d, iters, sink, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        rates.append(ops / (a.elapsed_time(b) / 1e3))
+    return {"lane_ops_per_s": float(statistics.median(rates)), "d": d, "iters": iters, "launches": reps}
+
+
 # ---- our arm ------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -343,11 +360,16 @@ def run_ours(args):
     alg_ops = (executed + checks) * 2 * d
     achieved = alg_ops / dom_avg_s if dom_avg_s else 0.0
     traffic = profiled_traffic(args.workload)
+    probe = measure_test_peak(G, torch, int(d), dev, stream)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "Tops/s", "frac": achieved / peak_ops if peak_ops else None,
                 "traffic": traffic,
                 "kernel": "k_dominance", "peak_basis": f"{props.multi_processor_count} SMs x "
                 f"{alu_lanes_per_sm} ALU-pipe lanes x {sm_max:.0f} MHz (max SM clock)",
+                "peak_measured": probe["lane_ops_per_s"] / 1e12,
+                "frac_of_measured": achieved / probe["lane_ops_per_s"] if probe["lane_ops_per_s"] else None,
+                "peak_measured_basis": f"dominance-test probe (gres_test_peak_probe), d={int(d)}, "
+                f"16 register-held candidates per thread, one wave, median of {probe['launches']} launches",
                 "ops_per_launch": alg_ops, "avg_launch_ms": dom_avg_s * 1e3 if dom_avg_s else None}
 
     # end to end through the host-buffer ABI: pinned input, H2D + compute + D2H each step

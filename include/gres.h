@@ -386,6 +386,24 @@ gres_status gres_compute_static(const uint32_t *d_data, int64_t n, int32_t d, in
                                 int64_t *d_sky_count, int64_t *h_sky_count, void *stream);
 size_t gres_static_scratch_bytes(void);
 
+/* Measurement helper: the peak rate of the dominance test (Def. 1) on this
+ * GPU, the denominator of the grid-dominance kernel's roofline. Queues one
+ * kernel on `stream` in which every thread holds 16 candidate rows in
+ * registers and tests each against a target cell [lo, hi] that moves every
+ * iteration, for `iters` iterations; a test is d "<=" and d "<" comparisons
+ * folded into one predicate, the 2d compare lane-ops per test that the
+ * grid-dominance kernel counts as its work. *lane_ops receives the compare
+ * lane-ops of the launch (blocks x 256 threads x iters x 16 x 2d); time the
+ * launch with CUDA events on `stream` for lane-ops/s.
+ *   d       1..8;  iters >= 1;  blocks: grid size, 0 = one full wave (as
+ *           many blocks as are resident on all SMs at once).
+ *   d_sink  device, one uint64: written only if a count reaches a value it
+ *           cannot reach (it keeps the tests from being optimised away).
+ * Errors: GRES_EINVAL for d outside [1, 8], iters < 1, blocks < 0, or a NULL
+ * pointer; GRES_ECUDA if the launch fails. */
+gres_status gres_test_peak_probe(int32_t d, int32_t iters, int32_t blocks, unsigned long long *d_sink,
+                                 void *stream, double *lane_ops);
+
 /* Host helper: the multiply-high constants gres_gproj uses for divisor
  * `delta` (>= 1): floor(v / delta) = (t + ((v - t) >> s1)) >> s2 with
  * t = mulhi(m, v). Exposed so the constants can be checked without a GPU. */

@@ -550,6 +550,16 @@ gres_status gres_gproj(const uint32_t *d_values, int64_t count, const uint32_t *
     return GRES_OK;
 }
 
+gres_status gres_test_peak_probe(int32_t d, int32_t iters, int32_t blocks, unsigned long long *d_sink,
+                                 void *stream, double *lane_ops) {
+    if (d < 1 || d > gres::kMaxD) return fail(GRES_EINVAL, "d must be in [1, 8]");
+    if (iters < 1 || blocks < 0) return fail(GRES_EINVAL, "iters must be >= 1 and blocks >= 0");
+    if (!d_sink || !lane_ops) return fail(GRES_EINVAL, "d_sink / lane_ops is NULL");
+    cudaError_t e = gres::launch_test_peak(d, iters, blocks, d_sink, static_cast<cudaStream_t>(stream), lane_ops);
+    if (e != cudaSuccess) return cuda_fail(e, "test peak probe");
+    return GRES_OK;
+}
+
 gres_status gres_udiv_magic(uint32_t delta, uint32_t *m, uint32_t *s1, uint32_t *s2) {
     if (delta < 1 || !m || !s1 || !s2) return fail(GRES_EINVAL, "delta must be >= 1, outputs non-NULL");
     gres::udiv_magic(delta, m, s1, s2);

@@ -268,6 +268,9 @@ cudaError_t launch_upload_steps(uint32_t *d_steps, uint32_t *d_magic, unsigned *
                                 int k, cudaStream_t st);
 cudaError_t launch_gproj(const uint32_t *d_values, int64_t count, const uint32_t *h_steps, int k,
                          uint32_t *d_out, cudaStream_t st);
+// The dominance-test peak probe (probe.cu); *lane_ops = its compare lane-ops.
+cudaError_t launch_test_peak(int d, int iters, int blocks, unsigned long long *sink, cudaStream_t st,
+                             double *lane_ops);
 
 }  // namespace gres
 

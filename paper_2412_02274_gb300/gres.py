@@ -94,6 +94,7 @@ def load():
                                        _p, _p, _p, _p]
         lib.gres_udiv_magic.argtypes = [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                                         ctypes.POINTER(_u32)]
+        lib.gres_test_peak_probe.argtypes = [_i32, _i32, _i32, _p, _p, ctypes.POINTER(ctypes.c_double)]
         lib.gres_launch_count.restype = ctypes.c_ulonglong
         lib.gres_launch_count.argtypes = []
         lib.gres_timing_enable.argtypes = [_i32]
@@ -130,7 +131,7 @@ def load():
                      "gres_timing_enable", "gres_timing_read", "gres_dataset_create",
                      "gres_dataset_destroy", "gres_dataset_info", "gres_dataset_sky_idx",
                      "gres_query_workspace_size", "gres_query", "gres_batch_workspace_size",
-                     "gres_batch"):
+                     "gres_batch", "gres_test_peak_probe"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -176,6 +177,15 @@ def udiv_magic(delta: int):
     m, s1, s2 = _u32(0), _u32(0), _u32(0)
     _check(load().gres_udiv_magic(int(delta), ctypes.byref(m), ctypes.byref(s1), ctypes.byref(s2)))
     return int(m.value), int(s1.value), int(s2.value)
+
+
+def test_peak_probe(d: int, iters: int, sink, blocks: int = 0, stream=None) -> float:
+    """Queue the dominance-test peak probe on ``stream``; returns the compare lane-ops of the
+    launch (time it with CUDA events on that stream). ``sink``: a CUDA tensor of >= 8 bytes."""
+    ops = ctypes.c_double(0.0)
+    _check(load().gres_test_peak_probe(int(d), int(iters), int(blocks), _ptr(sink), _stream_ptr(stream),
+                                       ctypes.byref(ops)))
+    return float(ops.value)
 
 
 # ---- torch-side helpers (device memory and streams) ---------------------------

@@ -161,3 +161,15 @@ def test_gres_reps_flag_rejected_where_not_supported():
     rc = lib.gres_compute(fake, 10, 2, 0, steps.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(bad),
                           fake, 1 << 30, fake, fake, None, ctypes.byref(cnt), None, None)
     assert rc == 1
+
+
+def test_test_peak_probe_argument_checks_need_no_gpu():
+    lib = G.load()
+    fake = ctypes.c_void_p(256)
+    ops = ctypes.c_double(0.0)
+    for d, iters, blocks, sink, out in [(0, 10, 0, fake, ops), (9, 10, 0, fake, ops), (4, 0, 0, fake, ops),
+                                        (4, 10, -1, fake, ops), (4, 10, 0, None, ops)]:
+        rc = lib.gres_test_peak_probe(d, iters, blocks, sink, None, ctypes.byref(out) if out is not None else None)
+        assert rc == 1, (d, iters, blocks)
+    rc = lib.gres_test_peak_probe(4, 10, 0, fake, None, None)
+    assert rc == 1 and b"NULL" in lib.gres_last_error()
