@@ -196,7 +196,7 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.surv_rows = static_cast<uint32_t *>(take(4 * DP * nn));
     w.surv_orig = static_cast<uint32_t *>(take(4 * nn));
     w.reps = static_cast<uint32_t *>(take(4 * DP * kMaxReps));
-    w.sel_hist = static_cast<uint32_t *>(take(4 * 2 * 4096));
+    w.sel_hist = static_cast<uint32_t *>(take(sizeof(uint32_t) * gres::kSelHistWords));
     w.rep_idx = static_cast<uint32_t *>(take(4 * kMaxReps));
     w.sky_rows = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.cand = static_cast<uint32_t *>(take(4 * DP * rows_pad));

@@ -69,7 +69,7 @@ struct Workspace {
     uint32_t *surv_rows;          // n * DP canonical rows, sum order
     uint32_t *surv_orig;          // n original row numbers, sum order
     uint32_t *reps;               // kMaxReps * DP
-    uint32_t *sel_hist;           // 2 * 4096 selection histogram counters
+    uint32_t *sel_hist;           // kSelHistWords selection histogram counters (zeroed with the header)
     uint32_t *rep_idx;            // kMaxReps representative candidate rows
     uint32_t *sky_rows;           // (n + tile) * DP canonical rows, skyline order
     uint32_t *cand;               // (n + tile) * DP canonical rows, partition order
@@ -86,6 +86,16 @@ struct Workspace {
 int64_t sort_blocks(int64_t n);
 int64_t scan_blocks(int64_t n);
 size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws);
+
+// Counters of the representative selection's two histogram levels (4,096 each).
+constexpr int kSelHistWords = 2 * 4096;
+
+// Zeroes the selection histograms (one thread block); done by the kernel that
+// resets the header, so no separate memset precedes the skyline pass.
+__device__ __forceinline__ void clear_sel_hist(uint32_t *sel) {
+    if (sel)
+        for (int i = threadIdx.x; i < kSelHistWords; i += blockDim.x) sel[i] = 0u;
+}
 
 // Resets the per-call header fields (one thread block, >= 32 threads).
 __device__ __forceinline__ void init_header(WsHeader *h, long long n) {

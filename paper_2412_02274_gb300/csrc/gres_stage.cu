@@ -87,8 +87,9 @@ constexpr int kRawLarge = 8000;
 // falls in one cell and nothing dominates).
 template <int CAP>
 __global__ void k_upload_steps(RawSteps<CAP> c, uint32_t *steps, uint32_t *magic, WsHeader *h, long long n,
-                               unsigned *zero, int gbits) {
+                               unsigned *zero, int gbits, uint32_t *sel) {
     if (h) init_header(h, n);
+    clear_sel_hist(sel);
     if (zero && threadIdx.x == 0) *zero = 0u;
     for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
         const uint32_t v = c.e[i];
@@ -102,13 +103,13 @@ __global__ void k_upload_steps(RawSteps<CAP> c, uint32_t *steps, uint32_t *magic
 // Queues the uploads of k steps (the first launch also resets the header h
 // and/or clears *zero when given).
 cudaError_t upload_steps(const uint32_t *h_steps, int k, uint32_t *steps, uint32_t *magic, WsHeader *h,
-                         long long n, unsigned *zero, int gbits, cudaStream_t st) {
+                         long long n, unsigned *zero, int gbits, uint32_t *sel, cudaStream_t st) {
     if (k <= kRawSmall) {
         RawSteps<kRawSmall> c;
         c.off = 0;
         c.count = k;
         std::memcpy(c.e, h_steps, sizeof(uint32_t) * (size_t)k);
-        k_upload_steps<kRawSmall><<<1, 256, 0, st>>>(c, steps, magic, h, n, zero, gbits); note_launch();
+        k_upload_steps<kRawSmall><<<1, 256, 0, st>>>(c, steps, magic, h, n, zero, gbits, sel); note_launch();
         return cudaGetLastError();
     }
     static RawSteps<kRawLarge> c;   // 32 KB: not on the stack
@@ -119,7 +120,8 @@ cudaError_t upload_steps(const uint32_t *h_steps, int k, uint32_t *steps, uint32
         c.count = std::min(kRawLarge, k - off);
         std::memcpy(c.e, h_steps + off, sizeof(uint32_t) * (size_t)c.count);
         k_upload_steps<kRawLarge><<<1, 256, 0, st>>>(c, steps, magic, off == 0 ? h : nullptr, n,
-                                                     off == 0 ? zero : nullptr, gbits); note_launch();
+                                                     off == 0 ? zero : nullptr, gbits,
+                                                     off == 0 ? sel : nullptr); note_launch();
     }
     return cudaGetLastError();
 }
@@ -1175,12 +1177,12 @@ cudaError_t dominance_batch_d(int slots, const DomQuery *qs, int count, unsigned
 
 cudaError_t launch_upload_steps(uint32_t *d_steps, uint32_t *d_magic, unsigned *zero, const uint32_t *h_steps,
                                 int k, cudaStream_t st) {
-    return upload_steps(h_steps, k, d_steps, d_magic, nullptr, 0, zero, 0, st);
+    return upload_steps(h_steps, k, d_steps, d_magic, nullptr, 0, zero, 0, nullptr, st);
 }
 
 cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st,
                               int gbits) {
-    return upload_steps(h_steps, k, ws.steps, ws.magic, ws.hdr, (long long)n, nullptr, gbits, st);
+    return upload_steps(h_steps, k, ws.steps, ws.magic, ws.hdr, (long long)n, nullptr, gbits, ws.sel_hist, st);
 }
 
 cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st) {

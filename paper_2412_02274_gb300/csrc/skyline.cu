@@ -122,7 +122,10 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t *total) {
     return before + incl - v;
 }
 
-__global__ void k_init(WsHeader *h, long long n) { init_header(h, n); }
+__global__ void k_init(WsHeader *h, long long n, uint32_t *sel) {
+    init_header(h, n);
+    clear_sel_hist(sel);
+}
 
 __device__ __forceinline__ void warp_minmax_atomic(unsigned long long kmin, unsigned long long kmax,
                                                    WsHeader *h) {
@@ -146,6 +149,7 @@ __device__ __forceinline__ void warp_minmax_atomic(unsigned long long kmin, unsi
 // buckets, monotone in f, relative width 1/64). Level 2 splits the bucket
 // where the running count passes R into up to 4,096 equal sub-buckets.
 constexpr int kSelBuckets = 4096;
+static_assert(2 * kSelBuckets == kSelHistWords, "two histogram levels in the workspace's counters");
 
 __device__ __forceinline__ uint32_t fbucket(unsigned long long f) {
     if (f < 128ull) return (uint32_t)f;
@@ -226,62 +230,6 @@ k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys, WsH
     }
 }
 
-// Level 2 and the gather in one pass: rows below bucket b1 are representatives
-// at once; rows in b1 are counted per sub-bucket and listed (boundary list,
-// capacity n). The last block finds the sub-bucket threshold and adds the
-// listed rows under it. At most R rows in all.
-__global__ void __launch_bounds__(1024)
-k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *hist, int R,
-         unsigned long long *bnd, uint32_t *rep_idx) {
-    __shared__ uint32_t sh[kSelBuckets];
-    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
-    __syncthreads();
-    const uint32_t b1 = h->sel_b1;
-    unsigned long long lo = 0;
-    int wbits = 0;
-    if (b1 < (uint32_t)kSelBuckets) fbucket_range(b1, &lo, &wbits);
-    const int sh2 = wbits > 12 ? wbits - 12 : 0;
-    unsigned *n_cand = reinterpret_cast<unsigned *>(&h->n_cand);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long f = keys[i];
-        const uint32_t b = fbucket(f);
-        if (b < b1) {
-            const unsigned pos = atomicAdd(n_cand, 1u);
-            if (pos < (unsigned)kMaxReps) rep_idx[pos] = (uint32_t)i;
-        } else if (b == b1) {
-            const uint32_t sb = (uint32_t)((f - lo) >> sh2);
-            atomicAdd(&sh[sb], 1u);
-            bnd[atomicAdd(&h->n_bnd, 1u)] = ((unsigned long long)sb << 32) | (unsigned long long)i;
-        }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
-        if (sh[b]) atomicAdd(&hist[b], sh[b]);
-    if (last_block_done(&h->done[1])) {
-        if (b1 >= (uint32_t)kSelBuckets) return;   // every row is a representative
-        const unsigned long long found = sel_find(hist, h->sel_below, R);
-        const unsigned long long thr = found == ~0ull ? ~0ull : (found >> 32);
-        const unsigned nb = h->n_bnd;
-        for (unsigned j = threadIdx.x; j < nb; j += blockDim.x) {
-            const unsigned long long v = bnd[j];
-            if ((v >> 32) < thr) {
-                const unsigned pos = atomicAdd(n_cand, 1u);
-                if (pos < (unsigned)kMaxReps) rep_idx[pos] = (uint32_t)(v & 0xFFFFFFFFull);
-            }
-        }
-    }
-}
-
-// Orders the representatives spatially -- by the Morton code of their rows
-// over their bounding box, then by row -- with a bitonic sort in one block
-// (compare-exchange steps with partners less than 32 apart through warp
-// shuffles, the others through shared memory), and writes their canonical
-// rows to `rows` in that order. Spatially tight runs of 32 representatives
-// let the filter skip whole runs. Representatives dominated by another
-// representative stay: by transitivity the filter drops exactly the same
-// rows with or without them. Also clears the filter's per-segment survivor
-// counts (nb of them).
 // Bitonic sort of one value per thread over a block of kMaxReps threads
 // (compare-exchange partners under 32 apart through warp shuffles, the others
 // through shared memory sk); returns this thread's value of the ascending
@@ -308,22 +256,28 @@ __device__ __forceinline__ unsigned long long block_bitonic(unsigned long long v
     return v;
 }
 
-// greps (may be NULL): also the 32 candidates of smallest f, canonical rows
-// padded with sentinel rows, for the gres stage's representatives.
+// Orders the representatives spatially -- by the Morton code of their rows
+// over their bounding box, then by row -- with a bitonic sort in one block,
+// and writes their canonical rows to `rows` in that order. Spatially tight
+// runs of 32 representatives let the filter skip whole runs. Representatives
+// dominated by another representative stay: by transitivity the filter drops
+// exactly the same rows with or without them. Also clears the filter's
+// per-segment survivor counts (nb of them). greps (may be NULL): also the 32
+// candidates of smallest f, canonical rows padded with sentinel rows, for the
+// gres stage's representatives. Run by one block of kMaxReps threads (all of
+// them); nc = the number of candidates in rep_idx; sk, xs, lo, hi: shared
+// arrays of kMaxReps, D * kMaxReps, D and D words.
 template <int D>
-__global__ void __launch_bounds__(kMaxReps)
-k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, uint32_t *rows,
-           uint32_t *blocksum, long long nb, uint32_t *greps) {
-    __shared__ unsigned long long sk[kMaxReps];
-    __shared__ uint32_t xs[D * kMaxReps];   // the candidates' canonical rows, attribute-major
-    __shared__ uint32_t lo[D], hi[D];
+__device__ __forceinline__ void rep_sort_block(const uint32_t *data, int dir, const uint32_t *rep_idx, int nc,
+                                               WsHeader *h, uint32_t *rows, uint32_t *blocksum, long long nb,
+                                               uint32_t *greps, unsigned long long *sk, uint32_t *xs,
+                                               uint32_t *lo, uint32_t *hi) {
     const int tid = threadIdx.x;
     for (long long j = tid; j < nb; j += kMaxReps) blocksum[j] = 0u;
-    const int nc = (int)min((long long)h->n_cand, (long long)kMaxReps);
     if (tid < D) { lo[tid] = 0xFFFFFFFFu; hi[tid] = 0u; }
     __syncthreads();
     uint32_t x[D];
-    const uint32_t idx = tid < nc ? rep_idx[tid] : 0xFFFFFFFFu;
+    const uint32_t idx = tid < nc ? __ldcg(rep_idx + tid) : 0xFFFFFFFFu;
     if (tid < nc) load_canon<D>(data, idx, dir, x);
     #pragma unroll
     for (int q = 0; q < D; q++) {
@@ -375,6 +329,68 @@ k_rep_sort(const uint32_t *data, int dir, const uint32_t *rep_idx, WsHeader *h, 
         h->n_cand = nc;
         h->n_reps = nc;
     }
+}
+
+// Level 2 and the gather in one pass: rows below bucket b1 are representatives
+// at once; rows in b1 are counted per sub-bucket and listed (boundary list,
+// capacity n). The last block finds the sub-bucket threshold, adds the listed
+// rows under it (at most R rows in all), and then orders the representatives
+// (rep_sort_block), so no separate launch is needed for that.
+template <int D>
+__global__ void __launch_bounds__(kMaxReps)
+k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *hist, int R,
+         unsigned long long *bnd, uint32_t *rep_idx, const uint32_t *data, int dir, uint32_t *rows,
+         uint32_t *blocksum, long long nb, uint32_t *greps) {
+    // the level-2 histogram, and in the last block the representative sort's arrays
+    constexpr size_t kHistBytes = sizeof(uint32_t) * kSelBuckets;
+    constexpr size_t kRepBytes = sizeof(unsigned long long) * kMaxReps + sizeof(uint32_t) * (D * kMaxReps + 2 * D);
+    __shared__ __align__(16) unsigned char raw[kHistBytes > kRepBytes ? kHistBytes : kRepBytes];
+    __shared__ unsigned nc_s;
+    uint32_t *sh = reinterpret_cast<uint32_t *>(raw);
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    const uint32_t b1 = h->sel_b1;
+    unsigned long long lo = 0;
+    int wbits = 0;
+    if (b1 < (uint32_t)kSelBuckets) fbucket_range(b1, &lo, &wbits);
+    const int sh2 = wbits > 12 ? wbits - 12 : 0;
+    unsigned *n_cand = reinterpret_cast<unsigned *>(&h->n_cand);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long f = keys[i];
+        const uint32_t b = fbucket(f);
+        if (b < b1) {
+            const unsigned pos = atomicAdd(n_cand, 1u);
+            if (pos < (unsigned)kMaxReps) rep_idx[pos] = (uint32_t)i;
+        } else if (b == b1) {
+            const uint32_t sb = (uint32_t)((f - lo) >> sh2);
+            atomicAdd(&sh[sb], 1u);
+            bnd[atomicAdd(&h->n_bnd, 1u)] = ((unsigned long long)sb << 32) | (unsigned long long)i;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
+        if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    if (!last_block_done(&h->done[1])) return;
+    if (b1 < (uint32_t)kSelBuckets) {   // else every row is a representative already
+        const unsigned long long found = sel_find(hist, h->sel_below, R);
+        const unsigned long long thr = found == ~0ull ? ~0ull : (found >> 32);
+        const unsigned nbnd = h->n_bnd;
+        for (unsigned j = threadIdx.x; j < nbnd; j += blockDim.x) {
+            const unsigned long long v = bnd[j];
+            if ((v >> 32) < thr) {
+                const unsigned pos = atomicAdd(n_cand, 1u);
+                if (pos < (unsigned)kMaxReps) rep_idx[pos] = (uint32_t)(v & 0xFFFFFFFFull);
+            }
+        }
+    }
+    __syncthreads();   // this block's gather (atomics, rep_idx stores) is done; sh is dead
+    if (threadIdx.x == 0) nc_s = atomicAdd(n_cand, 0u);
+    __syncthreads();
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(raw);
+    uint32_t *xs = reinterpret_cast<uint32_t *>(raw + sizeof(unsigned long long) * kMaxReps);
+    rep_sort_block<D>(data, dir, rep_idx, (int)min(nc_s, (unsigned)kMaxReps), h, rows, blocksum, nb, greps, sk,
+                      xs, xs + D * kMaxReps, xs + D * kMaxReps + D);
 }
 
 // Survivor flags (not dominated by any representative), rows in input order,
@@ -853,14 +869,12 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
                       int64_t *d_sky_idx, cudaStream_t st, bool gres_reps) {
     const long long nb = (n + kCB - 1) / kCB;
     const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 4);
-    cudaError_t e = cudaMemsetAsync(ws.sel_hist, 0, sizeof(uint32_t) * 2 * kSelBuckets, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;   // the selection histograms were zeroed with the header
     const int hb = (int)std::min<long long>((n + 1023) / 1024, 152LL * 2);
     k_keys<D><<<hb, 1024, 0, st>>>(d_data, n, dir, ws.keys[0], ws.hdr, ws.sel_hist, reps); note_launch();
-    k_sel_l2<<<hb, 1024, 0, st>>>(ws.keys[0], n, ws.hdr, ws.sel_hist + kSelBuckets, reps, ws.keys[1],
-                                  ws.rep_idx); note_launch();
-    k_rep_sort<D><<<1, kMaxReps, 0, st>>>(d_data, dir, ws.rep_idx, ws.hdr, ws.reps, ws.blocksum, nb,
-                                          gres_reps ? ws.greps : nullptr); note_launch();
+    k_sel_l2<D><<<hb, kMaxReps, 0, st>>>(ws.keys[0], n, ws.hdr, ws.sel_hist + kSelBuckets, reps, ws.keys[1],
+                                         ws.rep_idx, d_data, dir, ws.reps, ws.blocksum, nb,
+                                         gres_reps ? ws.greps : nullptr); note_launch();
     static int filter_blocks = 0;   // resident blocks of k_filter<D> on this GPU
     if (filter_blocks == 0) {
         int per_sm = 0, dev = 0, sms = 0;
@@ -902,7 +916,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
 int64_t scan_blocks(int64_t n) { return (n + kCB - 1) / kCB; }
 
 cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st) {
-    k_init<<<1, 32, 0, st>>>(ws.hdr, (long long)n); note_launch();
+    k_init<<<1, 256, 0, st>>>(ws.hdr, (long long)n, ws.sel_hist); note_launch();
     return cudaGetLastError();
 }
 

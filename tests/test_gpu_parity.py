@@ -145,18 +145,24 @@ def test_large_skyline_streams_from_global_memory(n):
     np.testing.assert_array_equal(gr[targets], exp)
 
 
-@pytest.mark.parametrize("d,n_plane,n_dom", [(5, 150000, 100000), (6, 200000, 150000), (8, 120000, 100000)])
-def test_large_path_many_survivors(d, n_plane, n_dom):
+@pytest.mark.parametrize("d,n_plane,n_dom,direction", [(5, 150000, 100000, G.MIN), (6, 200000, 150000, G.MIN),
+                                                      (8, 120000, 100000, G.MIN), (7, 140000, 60000, G.MAX)])
+def test_large_path_many_survivors(d, n_plane, n_dom, direction):
     """More than 131,072 filter survivors on the multi-kernel path (finer survivor keys, up to
     four digit passes): the planted skyline exactly, and gres of sampled skyline tuples
-    against the oracle over the whole skyline."""
+    against the oracle over the whole skyline. Larger-is-better takes the planted data
+    mirrored inside 20 bits (v -> 2^20 - 1 - v), which keeps the same skyline rows."""
     from planted import planted_skyline
     data, sky = planted_skyline(n_plane, n_dom, d, seed=d)
+    if direction == G.MAX:
+        assert int(data.max()) < (1 << 20)
+        data = ((1 << 20) - 1 - data).astype(np.uint32)
     steps = steps_log(32, 16)
-    gs, gr = _gpu(data, steps, G.MIN, G.plan(G.PART_GRID))
+    gs, gr = _gpu(data, steps, direction, G.plan(G.PART_GRID))
     np.testing.assert_array_equal(gs, sky)
     pick = np.linspace(0, len(sky) - 1, 61).astype(np.int64)
-    exp = O.gres(data, steps, candidates=sky, targets=sky[pick], threads=THREADS)
+    exp = O.gres(data, steps, "min" if direction == G.MIN else "max", candidates=sky, targets=sky[pick],
+                 threads=THREADS)
     np.testing.assert_array_equal(gr[pick], exp)
 
 
