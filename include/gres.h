@@ -163,10 +163,16 @@ gres_status gres_compute(const uint32_t *d_data, int64_t n, int32_t d, int32_t d
  *   h_step_idx   host, capacity n int32
  *   h_sky_count  host int64 (required)
  * With pinned h_data the calling thread keeps up to 4 captured CUDA graphs,
- * keyed by (h_data, n, d, dir, widths, plan, d_ws, device). A call matching
- * one replays it on a library stream: one graph launch instead of a dozen
- * kernel launches. The replay reads h_data's current contents. Kernels
- * replayed this way are counted once by gres_launch_count, at capture. */
+ * keyed by (h_data, n, d, dir, widths, plan, d_ws, h_sky_idx, h_step_idx,
+ * device). A call matching one replays it on a library stream: one graph
+ * launch instead of a dozen kernel launches. The replay reads h_data's
+ * current contents. If h_sky_idx and h_step_idx are pinned too, the graph
+ * also copies the first S0 results back, S0 being the skyline size of the
+ * call that captured it: a replay with S <= S0 then waits once, and one with
+ * S > S0 copies the rest and waits again. Positions S .. S0-1 of the result
+ * buffers (inside their capacity n) may then be overwritten with stale values.
+ * Kernels replayed this way are counted once by gres_launch_count, at
+ * capture. */
 gres_status gres_workspace_size_host(int64_t n, int32_t d, int32_t k, size_t *bytes);
 gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int32_t dir,
                               const uint32_t *h_steps, int32_t k, const gres_plan_cfg *cfg,

@@ -376,6 +376,9 @@ struct HostGraph {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     int64_t *h_out = nullptr;     // pinned: [0] S, [1] the header's status word (low 32 bits)
+    int64_t *h_sky = nullptr;     // the caller's result buffers the graph copies into
+    int32_t *h_step = nullptr;
+    int64_t spec = 0;             // results the graph copies (the capturing call's S; 0 if unpinned)
     unsigned long long used = 0;
 };
 constexpr size_t kHostGraphs = 4;
@@ -427,6 +430,7 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
     if (pinned && k >= 1 && h_steps) {
         for (HostGraph &g : g_host_graphs)
             if (g.exec && g.h_data == h_data && g.n == n && g.d == d && g.dir == dir && g.d_ws == d_ws &&
+                g.h_sky == h_sky_idx && g.h_step == h_step_idx &&
                 g.device == device && std::memcmp(&g.cfg, &plan_key, sizeof(plan_key)) == 0 &&
                 g.steps.size() == (size_t)k && std::memcmp(g.steps.data(), h_steps, 4 * (size_t)k) == 0)
                 hit = &g;
@@ -461,6 +465,16 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
             g.cfg = plan_key;
             g.d_ws = d_ws;
             g.device = device;
+            g.h_sky = h_sky_idx;
+            g.h_step = h_step_idx;
+            // with pinned result buffers the graph also copies the first S results (S of this call)
+            cudaPointerAttributes ra, rb;
+            const bool out_pinned = cudaPointerGetAttributes(&ra, h_sky_idx) == cudaSuccess &&
+                                    ra.type == cudaMemoryTypeHost &&
+                                    cudaPointerGetAttributes(&rb, h_step_idx) == cudaSuccess &&
+                                    rb.type == cudaMemoryTypeHost;
+            cudaGetLastError();
+            g.spec = out_pinned ? S : 0;
             bool ok = cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) == cudaSuccess &&
                       cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) == cudaSuccess &&
                       cudaMallocHost(&g.h_out, 2 * sizeof(int64_t)) == cudaSuccess;
@@ -475,6 +489,11 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
                                                  g.st) == cudaSuccess;
                 if (body) body = cudaMemcpyAsync(g.h_out + 1, &reinterpret_cast<gres::WsHeader *>(d_ws)->status,
                                                  sizeof(unsigned), cudaMemcpyDeviceToHost, g.st) == cudaSuccess;
+                if (body && g.spec > 0)
+                    body = cudaMemcpyAsync(h_sky_idx, d_sky, 8 * (size_t)g.spec, cudaMemcpyDeviceToHost, g.st) ==
+                               cudaSuccess &&
+                           cudaMemcpyAsync(h_step_idx, d_res, 4 * (size_t)g.spec, cudaMemcpyDeviceToHost, g.st) ==
+                               cudaSuccess;
                 ok = cudaStreamEndCapture(g.st, &graph) == cudaSuccess && body;
             }
             if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
@@ -495,10 +514,13 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
             }
         }
     }
-    if (S > 0) {
-        cudaError_t e = cudaMemcpyAsync(h_sky_idx, d_sky, 8 * (size_t)S, cudaMemcpyDeviceToHost, st);
+    // results the replayed graph has not copied already
+    const int64_t from = hit ? std::min(S, hit->spec) : 0;
+    if (S > from) {
+        cudaError_t e = cudaMemcpyAsync(h_sky_idx + from, d_sky + from, 8 * (size_t)(S - from),
+                                        cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "result copy");
-        e = cudaMemcpyAsync(h_step_idx, d_res, 4 * (size_t)S, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(h_step_idx + from, d_res + from, 4 * (size_t)(S - from), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(e, "result copy");
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");

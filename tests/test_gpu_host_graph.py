@@ -49,3 +49,30 @@ def test_replays_follow_the_buffer_contents_and_the_widths():
         esky, eres = _expect(a, steps, "max")
         np.testing.assert_array_equal(sky, esky)
         np.testing.assert_array_equal(res, eres)
+
+
+@pytest.mark.parametrize("pinned_out", [True, False])
+def test_replays_with_more_or_fewer_results_than_the_capture(pinned_out):
+    """The graph copies back as many results as the capturing call had (pinned result buffers):
+    replays with a larger skyline copy the rest, smaller ones stop at S. Unpinned result buffers
+    take the plain copies."""
+    n, d = 5000, 4
+    small = make_dataset("uni", n, d, bits=20, seed=3)    # few skyline rows
+    large = make_dataset("ant", n, d, bits=20, seed=4)    # many
+    pinned = torch.empty((n, d), dtype=torch.int32).pin_memory()
+    if pinned_out:
+        out = (torch.empty(n, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory())
+    else:
+        out = (torch.empty(n, dtype=torch.int64), torch.empty(n, dtype=torch.int32))
+    steps = steps_log(96, 16)
+    ws = G.alloc_workspace(n, d, 96, host=True)
+    stream = torch.cuda.current_stream()
+    sizes = []
+    for data in (small, small, large, large, small, large):   # the first call captures with the small skyline
+        pinned.copy_(torch.from_numpy(data.view(np.int32)))
+        sky, res = G.gres_compute_host(pinned, steps, G.MIN, ws=ws, out=out, stream=stream)
+        esky, eres = _expect(data, steps)
+        np.testing.assert_array_equal(np.asarray(sky), esky)
+        np.testing.assert_array_equal(np.asarray(res), eres)
+        sizes.append(len(esky))
+    assert sizes[2] > sizes[0]
