@@ -5,14 +5,18 @@
 //               key f(t) = sum of the canonical values. f is monotone, so s
 //               dominates t implies f(s) < f(t).
 //   2. select:  the representatives of Representative Filtering (Sec. 3.1):
-//               the rows with the smallest f, found by a selection (two
-//               12-bit histogram rounds over f give a threshold leaving at
-//               most R rows below it), then sorted by (f, row). Those
-//               dominated by another representative are dropped.
+//               the rows with the smallest f, found by a selection (a
+//               range-free histogram of f by its leading bits, then 4,096
+//               sub-buckets of the boundary bucket, give a threshold leaving
+//               at most R rows below it), then ordered by the Morton code of
+//               their rows so that runs of 32 are spatially tight.
+//               Representatives dominated by another one stay: by
+//               transitivity the filter drops the same rows either way.
 //   3. filter:  every row, in input order, against the representatives.
-//   4. group:   the survivors in a spatial order (16-bit Morton code over
-//               their bounding box) in 32-row tiles with per-tile and
-//               per-1024-row minima.
+//   4. group:   the survivors in a spatial order (a Morton code over their
+//               bounding box: 16 bits, or at least 4 bits per attribute when
+//               more than 131,072 rows survive) in 32-row tiles with
+//               per-tile and per-1024-row minima.
 //   5. final:   each survivor against the survivors of every tile whose
 //               minimum is <= it in every attribute; it is in the skyline iff
 //               none dominates it. (If t is dominated, a skyline tuple
