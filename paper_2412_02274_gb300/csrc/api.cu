@@ -1,7 +1,8 @@
 // api.cu -- the extern "C" entry points of libgres (include/gres.h): argument
 // validation, workspace layout, stream handling and error reporting. All
 // computation is queued as CUDA kernels (skyline.cu, radix_sort.cu,
-// gres_stage.cu); nothing here computes a result on the host.
+// gres_stage.cu; the test-rate probe in probe.cu); nothing here computes a
+// result on the host.
 #include "gres_internal.cuh"
 
 #include <atomic>
