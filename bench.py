@@ -2,21 +2,26 @@
 
 One step = one gres_compute call over a resident synthetic dataset: the
 sort-by-sum skyline pass, the candidate partitioning and the tile-pruned
-grid-dominance kernel. Default workload: anticorrelated N=100,000, d=4, values
-in [0, 2^20), 256 log-spaced integer widths 1 .. 2^16, Grid partitioning with
-m=4 slices per attribute.
+grid-dominance kernel. Default workload: uniform N=1,000,000, d=6, values in
+[0, 2^20), 256 log-spaced integer widths 1 .. 2^16, Angular partitioning (m=2,
+32 partitions). The same line carries the Sliced (p=64) and no-partitioning
+arms of that configuration and the anticorrelated N=100,000, d=4 configuration
+(Grid m=4) as extra keys.
 
 Metric: effective grid-dominance tests per second. Effective tests of one
 step = S * sum_t min(k*(t) + 1, K): the (candidate, width) tests of the plain
 early-exit scan of Algorithm 1 with the skyline as candidates (S candidates at
-each width up to the exit width). It depends only on the result.
+each width up to the exit width). It depends only on the result. The line
+also gives executed_ops_per_s: the compare lane-ops the pruned kernel really
+ran, per step time.
 
-Prints one JSON line (rank 0). Timing: W warm-up steps; K timed steps, each
-bracketed by CUDA events on the launching stream, with a 256 MiB write
-flushing L2 between steps (outside the events); barrier + synchronize around
-the K steps; max over ranks. Under torchrun each rank runs its own dataset
-instance (seed = rank) on its own GPU: weak scaling, no collective on the
-data path.
+Prints one JSON line (rank 0). Timing: W warm-up steps; R repeats of exactly K
+timed steps (R sized so that the repeats last about --clock-seconds, for the
+clock sampler), each step bracketed by CUDA events on the launching stream,
+with a 256 MiB write flushing L2 between steps (outside the events); barrier +
+synchronize around each K steps; the median repeat, max over ranks. Under
+torchrun each rank runs its own dataset instance (seed = rank) on its own GPU:
+weak scaling, no collective on the data path.
 """
 from __future__ import annotations
 
@@ -47,7 +52,13 @@ WORKLOADS = {
     "uni-n1000000-d6-b20-k256-none": ("uni", 1_000_000, 6, 20, ("log", 256, 16), "none", 0, 0),
     "uni-n1000-d2-b16-k64-grid": ("uni", 1_000, 2, 16, ("lin", 64, 64), "grid", 0, 0),
 }
-DEFAULT_WORKLOAD = "ant-n100000-d4-b20-k256-grid-m4"
+DEFAULT_WORKLOAD = "uni-n1000000-d6-b20-k256-angular-m2"
+# arms printed in the same line as the workload: the same configuration with the other
+# partitioning schemes, and the other single-GPU configuration
+ARMS = {
+    "uni-n1000000-d6-b20-k256-angular-m2": ("uni-n1000000-d6-b20-k256-sliced-p64", "uni-n1000000-d6-b20-k256-none",
+                                            "ant-n100000-d4-b20-k256-grid-m4"),
+}
 MULTI_WORKLOADS = ("batch-512", "serve-10k", "sweep")
 SCHEMES = {"none": 0, "grid": 1, "angular": 2, "sliced": 3}
 METRIC = "effective grid-dominance tests/s (skyline + gres of every skyline tuple)"
@@ -156,52 +167,72 @@ def profiled_traffic(workload: str):
 
 
 # ---- the oracle on the host cores (baseline and reference arm) --------------------
-def oracle_rate(data, steps, sample: int, threads: int):
-    """Oracle effective tests/s: BNL skyline of the full dataset, then gres for a
-    fixed, evenly spaced sample of skyline tuples (all skyline tuples as
-    candidates); the gres time is scaled from the sample to all tuples."""
+def oracle_full(data, steps, threads: int):
+    """The oracle on the whole workload, measured: BNL skyline of every row, then gres of
+    every skyline tuple over the skyline as candidates (OpenMP over targets)."""
     from oracle import oracle as O
     t0 = time.perf_counter()
     sky = O.skyline_bnl(data)
     t_sky = time.perf_counter() - t0
-    S = len(sky)
-    take = min(sample, S)
-    targets = sky[np.linspace(0, S - 1, take).astype(np.int64)] if S else sky
     t0 = time.perf_counter()
-    res = O.gres(data, steps, candidates=sky, targets=targets, threads=threads)
+    res = O.gres(data, steps, candidates=sky, targets=sky, threads=threads)
     t_gres = time.perf_counter() - t0
-    K = len(steps)
-    scale = S / take if take else 0.0
-    eff = S * float(np.minimum(res.astype(np.int64) + 1, K).sum()) * scale
-    secs = t_sky + t_gres * scale
-    return {"value": eff / secs if secs > 0 else 0.0, "seconds_estimated_full": secs,
-            "seconds_run": t_sky + t_gres, "S": S, "sample_targets": take}
+    eff = effective_tests(res, len(steps))
+    secs = t_sky + t_gres
+    return {"value": eff / secs if secs > 0 else 0.0, "seconds": secs, "skyline_s": t_sky,
+            "gres_s": t_gres, "S": len(sky), "effective_tests": eff}
 
 
 def run_reference(args):
+    """The oracle as the reference arm. The skyline (BNL over every row) is computed and
+    timed once before the warm-up. Step i then runs the oracle's gres for the skyline
+    tuples j with j % Q == i % Q (a rotating, evenly spread slice; Q = --ref-slices), so
+    that Q consecutive steps cover the whole workload once. Each step's time is its
+    measured gres time plus Q-th of the measured skyline time; the value is the effective
+    tests of the timed steps over their summed time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import oracle as O
     threads = os.cpu_count() or 1
     data, steps, *_ = workload_inputs(args.workload, 0)
-    for _ in range(args.warmup):
-        oracle_rate(data, steps, args.ref_sample, threads)
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        r = oracle_rate(data, steps, args.ref_sample, threads)
-        vals.append(r["value"])
-        secs += r["seconds_estimated_full"]
-    value = statistics.mean(vals)
+    K = len(steps)
+    t0 = time.perf_counter()
+    sky = O.skyline_bnl(data)
+    skyline_s = time.perf_counter() - t0
+    S = len(sky)
+    Q = max(1, min(args.ref_slices, S)) if S else 1
+
+    def step(i):
+        tg = sky[(i % Q)::Q]
+        t = time.perf_counter()
+        r = O.gres(data, steps, candidates=sky, targets=tg, threads=threads)
+        dt = time.perf_counter() - t + skyline_s / Q
+        return dt, S * int(np.minimum(r.astype(np.int64) + 1, K).sum())
+
+    for i in range(args.warmup):
+        step(i)
+    secs, units, per = 0.0, 0, []
+    for i in range(args.steps):
+        dt, u = step(i)
+        secs += dt
+        units += u
+        per.append(dt)
+    value = units / secs if secs > 0 else 0.0
+    sample = (f"BNL skyline of all {len(data)} rows (measured once: {skyline_s:.2f} s, charged 1/{Q} per "
+              f"step), then per step gres of every {Q}-th skyline tuple (rotating offset; S={S}) against "
+              f"all S; {Q} consecutive steps cover the whole workload")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"BNL skyline of all rows + gres of {r['sample_targets']} evenly "
-                                   f"spaced skyline tuples (of S={r['S']}), time scaled to all S"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "step_s": {"min": min(per) if per else None, "median": statistics.median(per) if per else None,
+                   "max": max(per) if per else None},
+        "skyline_s": skyline_s,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -235,6 +266,14 @@ def whole_job(total_ms: float, units: float, device):
     return t, u, (u / (t / 1e3) if t > 0 else 0.0)
 
 
+def repeats_for(target_s: float, est_repeat_ms: float, lo: int = 1, hi: int = 400) -> int:
+    """Repeats of the K-step timed loop that keep the GPU busy for about target_s seconds
+    (so the clock sampler sees the timed region), clamped to [lo, hi]."""
+    if target_s <= 0 or est_repeat_ms <= 0:
+        return lo
+    return int(max(lo, min(hi, round(target_s * 1e3 / est_repeat_ms))))
+
+
 def measure_test_peak(G, torch, d: int, dev, stream, iters: int = 4096, reps: int = 5) -> dict:
     """Measured peak of the dominance test on this GPU: the library's probe kernel (every
     thread tests 16 register-held candidates per iteration, 2d compare lane-ops each), one
@@ -255,7 +294,139 @@ def measure_test_peak(G, torch, d: int, dev, stream, iters: int = 4096, reps: in
     return {"lane_ops_per_s": float(statistics.median(rates)), "d": d, "iters": iters, "launches": reps}
 
 
+def alu_peak(torch, dev, clocks) -> tuple[float, str]:
+    """The ALU-pipe peak in lane-ops/s: integer compare / logic / min-max issue to the ALU
+    pipe, 16 lanes per clock per SM sub-partition, 64 per SM, at the maximum SM clock."""
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    lanes = 64
+    return (props.multi_processor_count * lanes * sm_max * 1e6,
+            f"{props.multi_processor_count} SMs x {lanes} ALU-pipe lanes x {sm_max:.0f} MHz (max SM clock)")
+
+
 # ---- our arm ------------------------------------------------------------------------
+class Arm:
+    """One workload on the device: the dataset resident in HBM, a workspace, one CUDA graph
+    of one gres_compute per timed step (or direct calls), the result of the warm-up and the
+    counters of a separate counted run."""
+
+    def __init__(self, G, torch, name, seed, dev, stream, steps, warmup, graph):
+        self.G, self.torch, self.name, self.dev, self.stream = G, torch, name, dev, stream
+        self.data, self.widths, self.scheme, self.m, self.p = workload_inputs(name, seed)
+        self.n, self.d = self.data.shape
+        self.K = len(self.widths)
+        self.cfg = G.plan(SCHEMES[self.scheme], m=self.m, p=self.p)
+        self.x = G.to_device_u32(self.data, dev)
+        self.ws = G.alloc_workspace(self.n, self.d, self.K)
+        self.out = (torch.empty(self.n, dtype=torch.int64, device=dev),
+                    torch.empty(self.n, dtype=torch.int32, device=dev),
+                    torch.zeros(1, dtype=torch.int64, device=dev))
+        for _ in range(warmup):
+            self.call(stream)
+        torch.cuda.synchronize(dev)
+        self.S = int(self.out[2].item())
+        self.step_idx = self.out[1][:self.S].cpu().numpy()
+        self.sky_idx = self.out[0][:self.S].cpu().numpy()
+        self.eff = effective_tests(self.step_idx, self.K)
+        # executed (candidate, width) lane-tests and pruning checks of the dominance kernel
+        tests = torch.zeros(2, dtype=torch.int64, device=dev)
+        cfg_c = G.plan(SCHEMES[self.scheme], m=self.m, p=self.p, count_tests=True)
+        G.gres_compute(self.x, self.widths, G.MIN, cfg_c, ws=self.ws, sync=False, out=self.out, stream=stream,
+                       tests=tests)
+        torch.cuda.synchronize(dev)
+        self.executed, self.checks = (int(v) for v in tests.cpu().tolist())
+        # stage events: each timed step replays its own captured graph, whose event record
+        # nodes give that step's stage durations (stage_times reads the last replay of
+        # each graph); timing stays on until then
+        G.timing_enable(True)
+        self.graphs = []
+        self.launches_per_call = None
+        if graph:
+            cap = torch.cuda.Stream(dev)
+            cap.wait_stream(stream)
+            for _ in range(steps):
+                g = torch.cuda.CUDAGraph()
+                c0 = G.launch_count()
+                with torch.cuda.graph(g, stream=cap):
+                    self.call(cap)
+                self.launches_per_call = G.launch_count() - c0
+                self.graphs.append(g)
+            torch.cuda.synchronize(dev)
+            for i in range(warmup):
+                self.graphs[i % len(self.graphs)].replay()
+            torch.cuda.synchronize(dev)
+        else:
+            G.timing_enable(False)
+
+    def call(self, stream):
+        self.G.gres_compute(self.x, self.widths, self.G.MIN, self.cfg, ws=self.ws, sync=False, out=self.out,
+                            stream=stream)
+
+    def timed_loop(self, steps, flush, world):
+        """Exactly `steps` steps, each bracketed by CUDA events on the launching stream, with
+        an L2 flush (a 256 MiB write) before each, outside the events; barrier +
+        synchronize on both sides. Returns (per-step ms, kernels launched)."""
+        import torch.distributed as dist
+        torch, G, stream, dev = self.torch, self.G, self.stream, self.dev
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        c0 = G.launch_count()
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record(stream)
+            if self.graphs:
+                self.graphs[i].replay()
+            else:
+                self.call(stream)
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        launches = (self.launches_per_call * steps) if self.graphs else G.launch_count() - c0
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)], launches
+
+    def check_result(self):
+        """The timed steps give the warm-up's result."""
+        assert int(self.out[2].item()) == self.S
+        assert np.array_equal(self.out[1][:self.S].cpu().numpy(), self.step_idx)
+
+    def stage_times(self, steps, flush, world):
+        """Per-stage (total ms, launches) of one timed loop, from the library's stage events:
+        with graphs, those of the last replay of each graph (the loop just run); with direct
+        calls, one more loop with timing on."""
+        G = self.G
+        if not self.graphs:
+            G.timing_enable(True)
+            self.timed_loop(steps, flush, world)
+        st = G.timing_read()
+        G.timing_enable(False)
+        return st
+
+    def summary(self, step_ms_mean, stages, peak_ops):
+        """The arm's numbers for the JSON line."""
+        dom_ms, dom_n = stages.get("dominance", (0.0, 0))
+        dom_avg_s = (dom_ms / dom_n) / 1e3 if dom_n else None
+        alg_ops = (self.executed + self.checks) * 2 * self.d
+        achieved = alg_ops / dom_avg_s if dom_avg_s else 0.0
+        return {"workload": self.name, "n": int(self.n), "d": int(self.d), "widths": self.K,
+                "scheme": self.scheme, "m": self.m, "p": self.p, "skyline_size": self.S,
+                "ms_per_step": step_ms_mean, "value": self.eff / (step_ms_mean / 1e3) if step_ms_mean else None,
+                "unit": UNIT, "effective_tests_per_step": self.eff,
+                "executed_lane_tests_per_step": self.executed, "pruning_checks_per_step": self.checks,
+                "executed_ops_per_s": alg_ops / (step_ms_mean / 1e3) if step_ms_mean else None,
+                "stage_ms_per_step": {k: (v[0] / v[1] if v[1] else None) for k, v in stages.items()},
+                "dominance": {"ops_per_launch": alg_ops, "avg_launch_ms": dom_avg_s * 1e3 if dom_avg_s else None,
+                              "achieved_tops": achieved / 1e12, "frac_of_alu_peak": achieved / peak_ops}}
+
+    def close(self):
+        self.graphs = []
+        self.x = self.ws = self.out = None
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -268,120 +439,56 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group(backend="nccl")
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
-
-    data, steps, scheme, m, p = workload_inputs(args.workload, seed=rank)
-    n, d = data.shape
-    K = len(steps)
-    cfg = G.plan(SCHEMES[scheme], m=m, p=p)
-    x = G.to_device_u32(data, dev)
-    ws = G.alloc_workspace(n, d, K)
-    out = (torch.empty(n, dtype=torch.int64, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
-           torch.zeros(1, dtype=torch.int64, device=dev))
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
-    for _ in range(args.warmup):
-        G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=stream)
-    torch.cuda.synchronize(dev)
-    S = int(out[2].item())
-    step_idx = out[1][:S].cpu().numpy()
-    eff = effective_tests(step_idx, K)
+    arm = Arm(G, torch, args.workload, rank, dev, stream, args.steps, args.warmup, args.graph)
+    n, d, K, S = arm.n, arm.d, arm.K, arm.S
 
-    # executed (candidate, width) lane-tests of the dominance kernel: a separate counted run
-    tests = torch.zeros(2, dtype=torch.int64, device=dev)
-    cfg_c = G.plan(SCHEMES[scheme], m=m, p=p, count_tests=True)
-    G.gres_compute(x, steps, G.MIN, cfg_c, ws=ws, sync=False, out=out, stream=stream, tests=tests)
-    torch.cuda.synchronize(dev)
-    executed, checks = (int(v) for v in tests.cpu().tolist())
-
-    # stage events: with --graph each timed step replays its own captured graph, whose
-    # captured event records give that step's stage durations
-    G.timing_enable(True)
-    G.timing_read()
-    graphs = []
-    launches_per_call = None
-    if args.graph:
-        cap = torch.cuda.Stream(dev)
-        cap.wait_stream(stream)
-        for _ in range(args.steps):
-            g = torch.cuda.CUDAGraph()
-            c0 = G.launch_count()
-            with torch.cuda.graph(g, stream=cap):
-                G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=cap)
-            launches_per_call = G.launch_count() - c0
-            graphs.append(g)
-        torch.cuda.synchronize(dev)
-        for i in range(args.warmup):
-            graphs[i % len(graphs)].replay()
-        torch.cuda.synchronize(dev)
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # Timed region: R repeats of exactly K steps (R sized so that the repeats keep the GPU
+    # busy for about --clock-seconds, long enough for the clock sampler to see them); the
+    # reported time is the median repeat.
+    probe_ms, _ = arm.timed_loop(args.steps, flush, world)
+    R = repeats_for(args.clock_seconds, float(sum(probe_ms)) * 1.3)
+    R = int(rank_max(R, dev))
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    launches0 = G.launch_count()
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        if graphs:
-            graphs[i].replay()
-        else:
-            G.gres_compute(x, steps, G.MIN, cfg, ws=ws, sync=False, out=out, stream=stream)
-        ends[i].record(stream)
-    torch.cuda.synchronize(dev)
-    launches = G.launch_count() - launches0
-    if graphs:
-        # replays launch the captured kernels; the library counted them at capture
-        launches = launches_per_call * args.steps
-    if world > 1:
-        dist.barrier()
+    rep_ms, launches = [], 0
+    for _ in range(R):
+        ms, l = arm.timed_loop(args.steps, flush, world)
+        rep_ms.append(float(sum(ms)))
+        launches = l
     clocks = sampler.stop()
-    stages = G.timing_read()
-    G.timing_enable(False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    # result check: the timed steps produce the same result as the warm-up
-    assert int(out[2].item()) == S and np.array_equal(out[1][:S].cpu().numpy(), step_idx)
-
-    total_ms, total_eff, value = whole_job(total_ms, float(eff) * args.steps, dev)
+    arm.check_result()
+    med_ms = float(statistics.median(rep_ms))
+    total_ms, total_eff, value = whole_job(med_ms, float(arm.eff) * args.steps, dev)
     ms_per_step = total_ms / args.steps
 
-    # roofline of the dominant kernel (the grid-dominance kernel)
-    dom_ms, dom_n = stages["dominance"]
-    dom_avg_s = (dom_ms / dom_n) / 1e3 if dom_n else None
-    props = torch.cuda.get_device_properties(dev)
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    # integer compare / logic / min-max issue to the ALU pipe: 16 lanes per clock per
-    # SM sub-partition, 64 per SM (ncu: that pipe at 88% while issue was at 56%)
-    alu_lanes_per_sm = 64
-    peak_ops = props.multi_processor_count * alu_lanes_per_sm * sm_max * 1e6
-    # 2d unsigned compares per (candidate, width) lane-test and per pruning check
-    alg_ops = (executed + checks) * 2 * d
-    achieved = alg_ops / dom_avg_s if dom_avg_s else 0.0
+    # stage durations of the dominant kernel (the grid-dominance kernel) and the others
+    stages = arm.stage_times(args.steps, flush, world)
+    peak_ops, peak_basis = alu_peak(torch, dev, clocks)
+    main = arm.summary(ms_per_step, stages, peak_ops)
+    dom = main["dominance"]
     traffic = profiled_traffic(args.workload)
     probe = measure_test_peak(G, torch, 4, dev, stream)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+    achieved = dom["achieved_tops"] * 1e12
+    roofline = {"bound": "alu", "achieved": dom["achieved_tops"], "peak": peak_ops / 1e12,
                 "unit": "Tops/s", "frac": achieved / peak_ops if peak_ops else None,
-                "traffic": traffic,
-                "kernel": "k_dominance", "peak_basis": f"{props.multi_processor_count} SMs x "
-                f"{alu_lanes_per_sm} ALU-pipe lanes x {sm_max:.0f} MHz (max SM clock)",
+                "traffic": traffic, "kernel": "k_dominance", "peak_basis": peak_basis,
                 "peak_measured": probe["lane_ops_per_s"] / 1e12,
                 "frac_of_measured": achieved / probe["lane_ops_per_s"] if probe["lane_ops_per_s"] else None,
                 "peak_measured_basis": f"dominance-test probe (gres_test_peak_probe), d={probe['d']}, "
                 f"16 register-held candidates per thread, one wave, median of {probe['launches']} launches",
-                "ops_per_launch": alg_ops, "avg_launch_ms": dom_avg_s * 1e3 if dom_avg_s else None}
+                "ops_per_launch": dom["ops_per_launch"], "avg_launch_ms": dom["avg_launch_ms"],
+                "ops_basis": "(executed lane-tests + pruning checks) x 2d unsigned compares, from a counted run"}
 
     # end to end through the host-buffer ABI: pinned input, H2D + compute + D2H each step
-    pinned = torch.from_numpy(data.view(np.int32)).pin_memory()
+    pinned = torch.from_numpy(arm.data.view(np.int32)).pin_memory()
     ws_h = G.alloc_workspace(n, d, K, host=True)
     hs = torch.empty(n, dtype=torch.int64).pin_memory()
     hr = torch.empty(n, dtype=torch.int32).pin_memory()
     for _ in range(max(1, args.warmup)):
-        G.gres_compute_host(pinned, steps, G.MIN, cfg, ws=ws_h, out=(hs, hr), stream=stream)
+        G.gres_compute_host(pinned, arm.widths, G.MIN, arm.cfg, ws=ws_h, out=(hs, hr), stream=stream)
     torch.cuda.synchronize(dev)
     # each call returns after its results are on the host, so host wall-clock time around it is
     # the call's end-to-end time; the L2 flush before each call stays outside the timed part
@@ -390,23 +497,43 @@ def run_ours(args):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        sk, rr = G.gres_compute_host(pinned, steps, G.MIN, cfg, ws=ws_h, out=(hs, hr), stream=stream)
+        sk, rr = G.gres_compute_host(pinned, arm.widths, G.MIN, arm.cfg, ws=ws_h, out=(hs, hr), stream=stream)
         e2e_total += time.perf_counter() - t0
     e2e_s = e2e_total / args.steps
-    assert np.array_equal(rr.numpy(), step_idx)
+    assert np.array_equal(rr.numpy(), arm.step_idx)
     e2e_s_all = rank_max(e2e_s, dev)
     e2e = {"value": total_eff / args.steps / e2e_s_all, "unit": UNIT,
            "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(S * 12 + 8),
            "ms_per_step": e2e_s_all * 1e3}
+    del ws_h, pinned
+
+    # the other arms of the same configuration and the other single-GPU configuration, on
+    # rank 0 (each with its own warm-up and K graph-replayed steps)
+    others = {}
+    if rank == 0 and not args.no_arms:
+        for name in ARMS.get(args.workload, ()):
+            a = Arm(G, torch, name, rank, dev, stream, args.steps, args.warmup, args.graph)
+            ms, _ = a.timed_loop(args.steps, flush, 1)
+            st = a.stage_times(args.steps, flush, 1)
+            a.check_result()
+            if a.data.shape == arm.data.shape and np.array_equal(a.data, arm.data) and \
+                    (a.S != S or not np.array_equal(a.step_idx, arm.step_idx)):
+                raise RuntimeError(f"{name}: results differ from {args.workload}")
+            others[name] = a.summary(float(sum(ms)) / args.steps, st, peak_ops)
+            a.close()
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        r = oracle_rate(data, steps, args.cpu_sample, threads)
+        r = oracle_full(arm.data, arm.widths, threads)
+        if r["S"] != S:
+            raise RuntimeError("oracle skyline size differs from the GPU's")
         cpu = {"value": r["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"BNL skyline of all {n} rows + gres of {r['sample_targets']} evenly spaced "
-                         f"skyline tuples (of S={r['S']}) against all S, gres time scaled to all S; "
-                         f"{r['seconds_run']:.1f} s of CPU wall time"}
+               "sample": f"the whole workload, measured: BNL skyline of all {n} rows ({r['skyline_s']:.2f} s) "
+                         f"+ gres of all S={r['S']} skyline tuples against all S ({r['gres_s']:.2f} s, "
+                         f"OpenMP over targets); {r['seconds']:.1f} s of CPU wall time",
+               "seconds": r["seconds"]}
 
     if rank == 0:
         line = {
@@ -414,21 +541,31 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "n": int(n), "d": int(d), "value_bits": WORKLOADS[args.workload][3],
-                       "widths": K, "scheme": scheme, "m": m, "p": p, "skyline_size": S,
-                       "effective_tests_per_step": eff, "executed_lane_tests_per_step": executed,
-                       "pruning_checks_per_step": checks,
+                       "widths": K, "scheme": arm.scheme, "m": arm.m, "p": arm.p, "skyline_size": S,
+                       "effective_tests_per_step": arm.eff, "executed_lane_tests_per_step": arm.executed,
+                       "pruning_checks_per_step": arm.checks,
                        "l2": "256 MiB write between timed steps (device-timed and end-to-end)",
                        "seed_per_rank": "rank",
                        "launch": "cuda graph replay" if args.graph else "direct calls",
+                       "timed_region": f"{R} repeats of exactly {args.steps} steps; the median repeat is reported",
                        "parallelism": f"replicas x{world} (one dataset per GPU)"},
+            "executed_ops_per_s": main["executed_ops_per_s"],
+            "effective_vs_executed": "value counts the tests of the plain early-exit scan (S candidates at "
+                                     "every width up to each exit); executed_ops_per_s counts the compare "
+                                     "lane-ops the pruned kernel actually ran, per step time",
             "gres_queries_per_s": world * 1e3 / ms_per_step,
-            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "stage_ms_per_step": main["stage_ms_per_step"],
+            "repeats": {"count": R, "ms_min": min(rep_ms), "ms_median": med_ms, "ms_max": max(rep_ms)},
             "roofline": roofline,
+            "arms": others,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
+            "launches_per_step": int(launches // max(args.steps, 1)),
             "clocks": clocks,
         }
+        if clocks.get("sm_mhz"):
+            line["cycles_per_step"] = ms_per_step * 1e-3 * clocks["sm_mhz"] * 1e6
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -779,8 +916,11 @@ def main(argv=None):
     ap.add_argument("--graph", action=argparse.BooleanOptionalAction, default=True,
                     help="each step replays a gres_compute captured in a CUDA graph "
                          "(--no-graph: direct calls)")
-    ap.add_argument("--cpu-sample", type=int, default=2048)
-    ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--no-arms", action="store_true", help="leave out the extra arms of the line")
+    ap.add_argument("--clock-seconds", type=float, default=2.0,
+                    help="repeat the K timed steps for about this long (the median repeat is reported)")
+    ap.add_argument("--ref-slices", type=int, default=4,
+                    help="reference arm: each step runs the oracle's gres for every Q-th skyline tuple")
     ap.add_argument("--tune-table", default="", help="batch-512: write the autotuned plan table (JSON) here")
     ap.add_argument("--chunk-targets", type=int, default=0,
                     help="serve-10k: targets per query piece (0: the library default)")

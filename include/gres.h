@@ -284,6 +284,12 @@ gres_status gres_serve_submit(gres_server *sv, int32_t dataset_id, const uint32_
  * finished in time (the ticket stays valid). */
 gres_status gres_serve_poll(gres_server *sv, uint64_t ticket, int32_t *h_step_idx, int64_t cap,
                             int64_t *h_sky_count, int64_t *h_latency_ns, int64_t timeout_us);
+/* The skyline row numbers of a served dataset, ascending (Def. 1): position j
+ * of every gres_serve_poll result on it is the tuple h_sky_idx[j]. Writes S
+ * to h_sky_count (may be NULL) and the S row numbers to h_sky_idx (host,
+ * capacity cap; GRES_EINVAL if cap < S). Waits for the copy. */
+gres_status gres_serve_sky_idx(gres_server *sv, int32_t dataset_id, int64_t *h_sky_idx, int64_t cap,
+                               int64_t *h_sky_count);
 /* Starts batches again after start_paused (or gres_serve_pause). */
 gres_status gres_serve_resume(gres_server *sv);
 /* Stops starting new batches (running ones finish; queries keep queueing). */

@@ -110,6 +110,29 @@ int64_t oracle_skyline_allpairs(const uint32_t *data, int64_t n, int d, int dir,
     return c;
 }
 
+/* Def. 1 read directly for chosen rows: flag[j] = 1 iff no tuple of r
+ * dominates row rows[j] (so flag[j] = 1 iff rows[j] is in Sky(r)). The same
+ * test as the all-pairs skyline, asked row by row, so that a large input can
+ * be checked on a sample of rows, or on every row with nthreads > 1 (OpenMP
+ * over the rows asked about; each answer is independent of the others). */
+void oracle_skyline_member(const uint32_t *data, int64_t n, int d, int dir,
+                           const int64_t *rows, int64_t nrows, int32_t *flag, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+    #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+#else
+    (void)nthreads;
+#endif
+    for (int64_t j = 0; j < nrows; j++) {
+        const uint32_t *t = data + rows[j] * d;
+        int dominated = 0;
+        for (int64_t y = 0; y < n && !dominated; y++)
+            if (oracle_dominates(data + y * d, t, d, dir)) dominated = 1;
+        flag[j] = !dominated;
+    }
+}
+
 /* ---- Sec. 2: grid projection, width form: floor(v / delta) -------------- */
 void oracle_gproj(const uint32_t *v, int64_t count, uint32_t delta, uint32_t *out)
 {

@@ -61,6 +61,9 @@ def _load():
             f = getattr(lib, name)
             f.restype = ctypes.c_int64
             f.argtypes = [_u32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _i64p]
+        lib.oracle_skyline_member.restype = None
+        lib.oracle_skyline_member.argtypes = [_u32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                              _i64p, ctypes.c_int64, _i32p, ctypes.c_int]
         lib.oracle_gproj.restype = None
         lib.oracle_gproj.argtypes = [_u32p, ctypes.c_int64, ctypes.c_uint32, _u32p]
         lib.oracle_gres.restype = None
@@ -134,6 +137,22 @@ def skyline_allpairs(data, direction="min") -> np.ndarray:
     c = _load().oracle_skyline_allpairs(_p(a, _u32p), len(a), a.shape[1], _dir(direction),
                                         _p(out, _i64p))
     return out[:c].copy()
+
+
+def skyline_member(data, rows=None, direction="min", threads=1) -> np.ndarray:
+    """Def. 1 row by row: a bool per asked row (default: every row), True iff no row of
+    ``data`` dominates it."""
+    a = _rows(data)
+    rw = _idx(rows, len(a))
+    out = np.empty(max(len(rw), 1), dtype=np.int32)
+    _load().oracle_skyline_member(_p(a, _u32p), len(a), a.shape[1], _dir(direction),
+                                  _p(rw, _i64p), len(rw), _p(out, _i32p), int(threads))
+    return out[:len(rw)].astype(bool)
+
+
+def skyline_threaded(data, direction="min", threads=1) -> np.ndarray:
+    """Sky(r) as ascending row numbers: Def. 1 asked for every row, OpenMP over the rows."""
+    return np.flatnonzero(skyline_member(data, None, direction, threads)).astype(np.int64)
 
 
 def gproj(values, delta: int) -> np.ndarray:

@@ -482,6 +482,34 @@ gres_status gres_serve_poll(gres_server *sv, uint64_t ticket, int32_t *h_step_id
     return GRES_OK;
 }
 
+gres_status gres_serve_sky_idx(gres_server *sv, int32_t dataset_id, int64_t *h_sky_idx, int64_t cap,
+                               int64_t *h_sky_count) {
+    if (!sv) return fail(GRES_EINVAL, "server is NULL");
+    const gres_dataset *ds = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->datasets.find(dataset_id);
+        if (it == sv->datasets.end()) return fail(GRES_EINVAL, "no such dataset");
+        ds = it->second.ds;
+        if (h_sky_count) *h_sky_count = it->second.S;
+        if (it->second.S > 0 && (!h_sky_idx || cap < it->second.S))
+            return fail(GRES_EINVAL, "index buffer too small (need sky_count)");
+        if (it->second.S == 0) return GRES_OK;
+        // the copy runs outside the lock; the caller keeps the dataset (no remove) meanwhile
+        it->second.pending++;
+    }
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    gres_status r = e == cudaSuccess ? gres_dataset_sky_idx(ds, h_sky_idx, 1, st) : cuda_fail(e, "serve stream");
+    if (st) cudaStreamDestroy(st);
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->datasets.find(dataset_id);
+        if (it != sv->datasets.end()) it->second.pending--;
+    }
+    return r;
+}
+
 gres_status gres_serve_resume(gres_server *sv) {
     if (!sv) return fail(GRES_EINVAL, "server is NULL");
     {

@@ -116,6 +116,7 @@ def load():
         lib.gres_serve_submit.argtypes = [_p, _i32, _p, _i32, ctypes.POINTER(ctypes.c_uint64)]
         lib.gres_serve_poll.argtypes = [_p, ctypes.c_uint64, _p, _i64, ctypes.POINTER(_i64),
                                         ctypes.POINTER(_i64), _i64]
+        lib.gres_serve_sky_idx.argtypes = [_p, _i32, _p, _i64, ctypes.POINTER(_i64)]
         lib.gres_serve_cancel.argtypes = [_p, ctypes.c_uint64]
         lib.gres_serve_resume.argtypes = [_p]
         lib.gres_serve_pause.argtypes = [_p]
@@ -123,7 +124,8 @@ def load():
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_size)]
         lib.gres_serve_destroy.argtypes = [_p]
         for name in ("gres_serve_create", "gres_serve_add_dataset", "gres_serve_remove_dataset",
-                     "gres_serve_submit", "gres_serve_poll", "gres_serve_cancel", "gres_serve_resume",
+                     "gres_serve_submit", "gres_serve_poll", "gres_serve_sky_idx", "gres_serve_cancel",
+                     "gres_serve_resume",
                      "gres_serve_pause", "gres_serve_stats", "gres_serve_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("gres_workspace_size", "gres_workspace_size_host", "sky_compute",
@@ -500,6 +502,18 @@ class Server:
             return None
         _check(rc)
         return out[: S.value].copy(), int(lat.value)
+
+    def sky_idx(self, dataset_id: int) -> np.ndarray:
+        """The dataset's skyline row numbers (ascending): the rows of every poll result."""
+        S = _i64(-1)
+        # a first call with no buffer reports S (and GRES_EINVAL when S > 0)
+        rc = self._lib.gres_serve_sky_idx(self._h, int(dataset_id), None, 0, ctypes.byref(S))
+        if S.value < 0:
+            _check(rc)
+        out = np.empty(max(S.value, 1), dtype=np.int64)
+        _check(self._lib.gres_serve_sky_idx(self._h, int(dataset_id), out.ctypes.data_as(ctypes.c_void_p),
+                                            len(out), ctypes.byref(S)))
+        return out[: S.value]
 
     def cancel(self, ticket: int) -> None:
         _check(self._lib.gres_serve_cancel(self._h, ctypes.c_uint64(ticket)))

@@ -213,6 +213,26 @@ def test_skyline_2d_staircase_and_1d():
     assert list(O.skyline_bnl(data)) == [1, 3]
 
 
+def test_skyline_member_row_by_row():
+    """Def. 1 asked row by row (the oracle's check for inputs too large for its BNL): on every
+    row it is the 2-D staircase and the BNL skyline, in both directions, with one thread or
+    many; on a sample of rows it answers each row as on the whole input."""
+    for seed in range(12):
+        data = make_dataset("uni", 400, 2, bits=6, seed=seed)
+        assert list(O.skyline_threaded(data, threads=1)) == _staircase_2d(data)
+        assert list(O.skyline_threaded(data, threads=4)) == _staircase_2d(data)
+    for dist, d in (("ant", 3), ("clu", 5), ("uni", 8), ("ant", 1)):
+        data = make_dataset(dist, 1500, d, bits=8, seed=d)
+        for direction in ("min", "max"):
+            full = O.skyline_member(data, direction=direction, threads=3)
+            assert list(np.flatnonzero(full)) == list(O.skyline_bnl(data, direction))
+            rows = np.array([0, 7, 7, 1499, 311, 42], np.int64)
+            assert list(O.skyline_member(data, rows, direction)) == list(full[rows])
+    # duplicates of a skyline row stay in it; a row strictly inside is out
+    data = np.array([[1, 2], [1, 2], [2, 3], [0, 5]], np.uint32)
+    assert list(O.skyline_member(data)) == [True, True, False, True]
+
+
 def test_planted_skyline_construction():
     """The planted construction (plane rows plus dominated offsets) has the plane rows as its
     skyline: checked against both oracle skylines, so the large GPU tests that rely on it
