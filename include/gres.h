@@ -389,7 +389,10 @@ gres_status gres_timing_read(double *ms, int64_t *launches, int32_t nstages);
  * cudaMalloc / cudaFree); keep gres_timing_enable off, since stage timing
  * creates CUDA events on first use. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture. All calls share the array:
+ * make that first call before any stream capture: a call that needs the
+ * lookup inside a capture gets GRES_EINVAL. The address is kept per device
+ * with the id of its CUDA context, and looked up again after the context
+ * changed (cudaDeviceReset). All calls share the array:
  * each call re-initialises what it needs, and calls that overlap on the GPU
  * (different streams or unsynchronised threads) race on it -- serialise them. */
 gres_status gres_compute_static(const uint32_t *d_data, int64_t n, int32_t d, int32_t dir,

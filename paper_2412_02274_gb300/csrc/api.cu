@@ -206,6 +206,7 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.perm = static_cast<uint32_t *>(take(4 * nn));
     w.res = static_cast<int32_t *>(take(4 * nn));
     w.greps = static_cast<uint32_t *>(take(4 * DP * 32));
+    w.kill = static_cast<uint32_t *>(take(4 * DP * kKillers));
     w.steps = static_cast<uint32_t *>(take(4 * (size_t)(k > 0 ? k : 1)));
     w.magic = static_cast<uint32_t *>(take(16 * (size_t)(k > 0 ? k : 1)));
     w.bytes = off;
@@ -435,6 +436,22 @@ gres_status gres_compute_host(const uint32_t *h_data, int64_t n, int32_t d, int3
                 g.device == device && std::memcmp(&g.cfg, &plan_key, sizeof(plan_key)) == 0 &&
                 g.steps.size() == (size_t)k && std::memcmp(g.steps.data(), h_steps, 4 * (size_t)k) == 0)
                 hit = &g;
+        if (hit && hit->spec > 0) {
+            // the graph copies results straight into the caller's buffers: they must still be
+            // pinned (a freed pinned buffer may come back as pageable memory at the same address)
+            cudaPointerAttributes ra, rb;
+            const bool out_pinned = cudaPointerGetAttributes(&ra, h_sky_idx) == cudaSuccess &&
+                                    ra.type == cudaMemoryTypeHost &&
+                                    cudaPointerGetAttributes(&rb, h_step_idx) == cudaSuccess &&
+                                    rb.type == cudaMemoryTypeHost;
+            cudaGetLastError();
+            if (!out_pinned) {
+                const size_t at = (size_t)(hit - g_host_graphs.data());
+                host_graph_free(*hit);
+                g_host_graphs.erase(g_host_graphs.begin() + (std::ptrdiff_t)at);
+                hit = nullptr;
+            }
+        }
     }
     int64_t S = 0;
     if (hit) {

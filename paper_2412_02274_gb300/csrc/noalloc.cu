@@ -13,14 +13,19 @@
 // The scratch is one file-scope __device__ array of kStaticScratchBytes. Every
 // GPU on which this library's kernels are loaded holds it until the process
 // exits. In host code the array's name is only a host-side stand-in, so its
-// device address is looked up once per device with cudaGetSymbolAddress (with
-// that device current) and cached; the first call on a device does that
-// lookup, which is why the first call should happen before any stream
+// device address is looked up with cudaGetSymbolAddress (with that device
+// current) and cached per device together with the id of the CUDA context it
+// belongs to; the first call on a device does that lookup, and so does the
+// first call after the context changed (a cudaDeviceReset destroys the
+// context, and the array's address with it). A lookup is refused inside a
+// stream capture, which is why the first call should happen before any
 // capture. All calls share the array: it keeps the previous call's contents
 // (every call re-initialises what must start at zero before using it), and
 // calls that overlap on the GPU -- two streams, or two host threads without
 // ordering -- race on it and must be serialised by the caller.
 #include "gres_internal.cuh"
+
+#include <cuda.h>   // CUcontext / CUresult only: the two driver calls are fetched at run time
 
 #include <cstdio>
 #include <mutex>
@@ -32,23 +37,76 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    void *addr = nullptr;
+    unsigned long long ctx = 0;   // id of the context the address belongs to (0: unknown)
+};
+ScratchAddr g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Device address of g_static_scratch on the current device (looked up once).
-cudaError_t scratch_address(void **out) {
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context, or 0 when there is none
+// (or the driver cannot say). A context created after a device reset gets a
+// new id. Neither driver call queues work or allocates, so this is safe
+// inside a stream capture.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_static_scratch on the current device: the cached one
+// while the context is unchanged, else looked up again (not inside a stream
+// capture: *capturing is set and cudaErrorStreamCaptureUnsupported returned).
+cudaError_t scratch_address(cudaStream_t st, void **out, bool *capturing) {
+    *capturing = false;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+    ScratchAddr &c = g_scratch[dev];
+    if (c.addr && ctx != 0 && c.ctx == ctx) {
+        *out = c.addr;
+        return cudaSuccess;
     }
-    *out = g_scratch_addr[dev];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        // no lookup inside a capture; without a context id the cached address is kept
+        if (c.addr && ctx == 0) {
+            *out = c.addr;
+            return cudaSuccess;
+        }
+        *capturing = true;
+        return cudaErrorStreamCaptureUnsupported;
+    }
+    cudaGetLastError();
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    c.addr = p;
+    c.ctx = current_context_id();   // the lookup made the context current if it was not
+    *out = p;
     return cudaSuccess;
 }
 
@@ -74,7 +132,12 @@ gres_status gres_compute_static(const uint32_t *d_data, int64_t n, int32_t d, in
         return gres::set_error(GRES_EINVAL, msg);
     }
     void *scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
+    bool capturing = false;
+    cudaError_t e = scratch_address(static_cast<cudaStream_t>(stream), &scratch, &capturing);
+    if (capturing)
+        return gres::set_error(GRES_EINVAL,
+                               "gres_compute_static: the first call on a device (or after a device reset) "
+                               "must come before any stream capture");
     if (e != cudaSuccess) {
         char msg[160];
         std::snprintf(msg, sizeof(msg), "gres_compute_static: cudaGetSymbolAddress: %s",
