@@ -746,10 +746,14 @@ def run_sweep(args):
             kw = {"m": mp} if scheme in ("grid", "angular") else ({"p": mp} if scheme == "sliced" else {})
             cfg = G.plan(SCHEMES[scheme], reps=reps, **kw)
             G.gres_compute_g(x, 20, glist, G.MIN, cfg, ws=ws, stream=stream)    # warm-up
-            tests = torch.zeros(2, dtype=torch.int64, device=dev)
-            cfg_c = G.plan(SCHEMES[scheme], reps=reps, count_tests=True, **kw)
+            # counters split by partition (GRES_FLAG_COUNT_PARTS): the paper's phases
+            cfg_c = G.plan(SCHEMES[scheme], reps=reps, count_parts=True, **kw)
+            P = G.plan_partitions(cfg_c, d)
+            tests = torch.zeros(2 + 4 * P, dtype=torch.int64, device=dev)
             sky, idx = G.gres_compute_g(x, 20, glist, G.MIN, cfg_c, ws=ws, stream=stream, tests=tests)
-            lane_tests, checks = (int(v) for v in tests.cpu().tolist())
+            tv = tests.cpu().numpy()
+            lane_tests, checks = int(tv[0]), int(tv[1])
+            split = tv[2:].reshape(P, 4)
             G.timing_enable(True)
             G.timing_read()
             t = []
@@ -766,6 +770,13 @@ def run_sweep(args):
             rows.append({"dist": dist, "n": n, "d": d, "p_target": p_target, "reps": reps or 1024,
                          "scheme": scheme, "param": mp, "partitions": cells, "S": S,
                          "lane_tests": lane_tests, "pruning_checks": checks,
+                         # the paper's accounting: parallel phase = the heaviest partition's work
+                         # against its own candidates, final phase = all work across partitions
+                         "parallel_phase_lane_tests": int(split[:, 0].max()),
+                         "final_phase_lane_tests": int(split[:, 2].sum()),
+                         "parallel_phase_row_checks": int(split[:, 1].max()),
+                         "final_phase_row_checks": int(split[:, 3].sum()),
+                         "local_lane_tests": int(split[:, 0].sum()),
                          "dense_tests": S * S * len(glist),
                          "ms": float(np.median(t)), "skyline_ms": st["skyline"][0] / max(st["skyline"][1], 1),
                          "partition_ms": st["partition"][0] / max(st["partition"][1], 1),

@@ -102,6 +102,27 @@ typedef struct {
  * (rejected by the dataset and server calls). With GRES_FLAG_COUNT_TESTS the
  * representative tests are counted in d_tests[0] too. */
 #define GRES_FLAG_GRES_REPS 2
+/* The paper's accounting of dominance tests by phase (Sec. 4: the parallel
+ * phase costs what its heaviest partition costs, the final phase what it
+ * tests across partitions), on this kernel's search: with this flag (and
+ * GRES_FLAG_COUNT_TESTS) d_tests holds 2 + 4 * P uint64, P =
+ * gres_plan_partitions(cfg, d), and for every target tuple in partition p the
+ * kernel adds to d_tests[2 + 4p + 0] its lane-tests against candidates of
+ * partition p, [+1] its row checks (one per candidate row looked at, per lane)
+ * of candidates of partition p, [+2] and [+3] the same against candidates of
+ * other partitions (padding rows of the last tile count there). Tile and
+ * super-tile bounding-box checks are not split: they stay in d_tests[1] only.
+ * Local work of a partition runs in parallel with the other partitions'; the
+ * cross-partition work is what the paper's final phase does. Honoured by
+ * gres_compute and gres_compute_g only (with GRES_FLAG_GRES_REPS the
+ * representative tests are not split either). */
+#define GRES_FLAG_COUNT_PARTS 4
+
+/* The number of partitions P of a plan for d attributes (after the defaults of
+ * gres_plan_cfg are applied): m^d for GRID, m^(d-1) for ANGULAR, p for SLICED,
+ * 1 for NONE -- the size of the per-partition counts of GRES_FLAG_COUNT_PARTS.
+ * cfg may be NULL (the default plan). GRES_EINVAL for a bad plan or d. */
+gres_status gres_plan_partitions(const gres_plan_cfg *cfg, int32_t d, int64_t *out);
 
 /* Thread-local message for the calling thread's most recent failed call
  * ("" if none). The pointer stays valid until the next call on that thread. */
@@ -418,6 +439,18 @@ size_t gres_static_scratch_bytes(void);
  * pointer; GRES_ECUDA if the launch fails. */
 gres_status gres_test_peak_probe(int32_t d, int32_t iters, int32_t blocks, unsigned long long *d_sink,
                                  void *stream, double *lane_ops);
+
+/* Check of the bounded grid-wide wait that the cooperative sorts (inputs above
+ * 131,072 rows) use between their phases; the paper has no counterpart. One
+ * cooperative launch of one block per SM waits at a grid-wide barrier, except
+ * block `absent` (-1: none), which leaves at once. The waiting blocks give up
+ * after about a second, set the timeout bit in the status word and return, so
+ * the GPU context stays usable. d_words: device, 3 uint32 (arrival count,
+ * generation, status), zeroed by the call; *h_status gets the status word
+ * (bit 0: a wait ran out). Waits for the launch.
+ * Returns GRES_OK, GRES_ETIMEOUT if a wait ran out, GRES_EINVAL for NULL
+ * pointers, GRES_ECUDA if a CUDA call fails. */
+gres_status gres_barrier_probe(int32_t absent, unsigned *d_words, void *stream, uint32_t *h_status);
 
 /* Host helper: the multiply-high constants gres_gproj uses for divisor
  * `delta` (>= 1): floor(v / delta) = (t + ((v - t) >> s1)) >> s2 with

@@ -71,7 +71,10 @@ gres_status check_plan(const gres_plan_cfg *cfg, int32_t d, gres_plan_cfg *out) 
     if (c.scheme < GRES_PART_NONE || c.scheme > GRES_PART_SLICED)
         return fail(GRES_EINVAL, "cfg.scheme must be a gres_part");
     if (c.reserved != 0) return fail(GRES_EINVAL, "cfg.reserved must be 0");
-    if (c.flags & ~(GRES_FLAG_COUNT_TESTS | GRES_FLAG_GRES_REPS)) return fail(GRES_EINVAL, "unknown cfg.flags bits");
+    if (c.flags & ~(GRES_FLAG_COUNT_TESTS | GRES_FLAG_GRES_REPS | GRES_FLAG_COUNT_PARTS))
+        return fail(GRES_EINVAL, "unknown cfg.flags bits");
+    if ((c.flags & GRES_FLAG_COUNT_PARTS) && !(c.flags & GRES_FLAG_COUNT_TESTS))
+        return fail(GRES_EINVAL, "GRES_FLAG_COUNT_PARTS needs GRES_FLAG_COUNT_TESTS");
     if (c.reps == 0) c.reps = gres::kMaxReps;
     if (c.reps < 1 || c.reps > gres::kMaxReps) return fail(GRES_EINVAL, "cfg.reps must be in [1, 1024]");
     if (c.slots == 0) c.slots = 8;
@@ -207,6 +210,7 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.res = static_cast<int32_t *>(take(4 * nn));
     w.greps = static_cast<uint32_t *>(take(4 * DP * 32));
     w.kill = static_cast<uint32_t *>(take(4 * DP * kKillers));
+    w.pid = static_cast<uint32_t *>(take(4 * (size_t)rows_pad));
     w.steps = static_cast<uint32_t *>(take(4 * (size_t)(k > 0 ? k : 1)));
     w.magic = static_cast<uint32_t *>(take(16 * (size_t)(k > 0 ? k : 1)));
     w.bytes = off;
@@ -262,6 +266,16 @@ gres_status gres_workspace_size_host(int64_t n, int32_t d, int32_t k, size_t *by
     if (s != GRES_OK) return s;
     const int64_t nn = n > 0 ? n : 1;
     *bytes += align256(4 * (size_t)nn * d) + align256(8 * (size_t)nn) + align256(4 * (size_t)nn) + 256;
+    return GRES_OK;
+}
+
+gres_status gres_plan_partitions(const gres_plan_cfg *cfg, int32_t d, int64_t *out) {
+    if (!out) return fail(GRES_EINVAL, "out is NULL");
+    if (d < 1 || d > gres::kMaxD) return fail(GRES_EINVAL, "d must be in [1, 8]");
+    gres_plan_cfg c;
+    gres_status s = check_plan(cfg, d, &c);
+    if (s != GRES_OK) return s;
+    *out = gres::plan_partitions(c, d);
     return GRES_OK;
 }
 

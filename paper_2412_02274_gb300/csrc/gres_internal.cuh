@@ -13,6 +13,7 @@ namespace gres {
 constexpr int kMaxD = 8;
 constexpr int kTileRows = 32;          // candidate rows per pruning tile
 constexpr int kMaxReps = 1024;         // skyline pre-filter representatives
+constexpr int kKillers = 32;           // representatives of the first, one-row-per-thread filter pass
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // padding row value: never dominates
 
 // Rows of canonical values are stored padded to DP words (16-byte multiples).
@@ -47,6 +48,10 @@ struct WsHeader {
     unsigned int slo[kMaxD];      // per-attribute canonical minimum over the survivors
     unsigned int shi[kMaxD];      // per-attribute canonical maximum over the survivors
     unsigned int n_bnd;           // rows in the selection's boundary bucket
+    unsigned int n_alive;         // rows left by the one-row-per-thread filter pass
+    unsigned int dlo[kMaxD];      // per-attribute canonical minimum over all rows
+    unsigned int dhi[kMaxD];      // per-attribute canonical maximum over all rows
+    unsigned int bar[2];          // grid-wide barrier of the cooperative sorts: arrivals, generation
 };
 
 // Digit passes that do work in the radix sort of the current key range; the
@@ -78,6 +83,8 @@ struct Workspace {
     uint32_t *perm;               // n: partition position -> skyline position
     int32_t *res;                 // n: per partition position, a bound on the result (GRES_FLAG_GRES_REPS)
     uint32_t *greps;              // 32 * DP: the gres-stage representatives (GRES_FLAG_GRES_REPS)
+    uint32_t *kill;               // kKillers * DP: the first filter pass's representatives
+    uint32_t *pid;                // n + tile: partition number per partition position (GRES_FLAG_COUNT_PARTS)
     uint32_t *steps;              // K widths
     uint32_t *magic;              // K * 4 multiply-high constants (m, s1, s2, delta)
     size_t bytes;
@@ -108,6 +115,8 @@ __device__ __forceinline__ void init_header(WsHeader *h, long long n) {
         h->n_reps = 0;
         h->n_cand = 0;
         h->n_bnd = 0;
+        h->n_alive = 0;
+        h->bar[0] = 0;
         h->work_next = 0;
         h->status = 0;
         h->sorted_sel = 0;
@@ -118,6 +127,8 @@ __device__ __forceinline__ void init_header(WsHeader *h, long long n) {
         h->hi[threadIdx.x] = 0u;
         h->slo[threadIdx.x] = 0xFFFFFFFFu;
         h->shi[threadIdx.x] = 0u;
+        h->dlo[threadIdx.x] = 0xFFFFFFFFu;
+        h->dhi[threadIdx.x] = 0u;
     }
 }
 
@@ -225,6 +236,15 @@ struct DomQuery {
     const int32_t *ub = nullptr;
 };
 
+// Optional per-partition counts of one query (GRES_FLAG_COUNT_PARTS): the
+// partition number of every partition position (padding positions: ~0) and
+// the counters (see include/gres.h), indexed from pcnt[2].
+struct PartCount {
+    const uint32_t *pid = nullptr;
+    unsigned long long *pcnt = nullptr;
+    unsigned nparts = 0;      // partitions: targets of a larger number are not counted
+};
+
 // Division constants to make on the device for one query (k_make_magic).
 struct MagicJob {
     const uint32_t *steps;
@@ -237,12 +257,12 @@ cudaError_t launch_init(Workspace &ws, int64_t n, cudaStream_t st);
 // Uploads the widths and their division constants and resets the header.
 cudaError_t launch_init_steps(Workspace &ws, int64_t n, const uint32_t *h_steps, int k, cudaStream_t st,
                               int gbits = 0);
-// Inputs of at most kClusterSortMax rows sort their survivors and their
-// skyline inside one thread-block cluster per sort (cluster.cuh); larger ones
-// with three grid-wide kernels per digit pass (launch_radix_sort).
+// Survivor sets and skylines of at most kClusterSortMax rows are sorted inside
+// one thread-block cluster per sort (cluster.cuh); larger ones in one
+// cooperative launch (radix.cuh). The counts are known on the device only: for
+// inputs above kClusterSortMax rows both are queued and each returns at once
+// when the count is not its size.
 constexpr int64_t kClusterSortMax = 131072;
-cudaError_t launch_radix_sort(Workspace &ws, int64_t n_max, const long long *d_n,
-                              int max_passes, cudaStream_t st);
 cudaError_t launch_skyline(const uint32_t *d_data, int64_t n, int d, int dir, int reps,
                            Workspace &ws, int64_t *d_sky_idx, cudaStream_t st, bool gres_reps = false);
 cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir, int k,
@@ -253,6 +273,9 @@ cudaError_t launch_gres_stage(const uint32_t *d_data, int64_t n, int d, int dir,
 // (ws.greps) dominates, into ws.res (GRES_FLAG_GRES_REPS); after the partitioning.
 cudaError_t launch_rep_bound(int d, int64_t n, Workspace &ws, int k, int dir, int gbits,
                              unsigned long long *tests, cudaStream_t st);
+// Partitions of a checked plan for d attributes (GRID m^d, ANGULAR m^(d-1),
+// SLICED p, NONE 1).
+int64_t plan_partitions(const gres_plan_cfg &cfg, int d);
 // The candidate partitioning of the skyline in ws (cand, tmin, perm).
 cudaError_t launch_partition(int d, const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st);
 // The caller's rows as the candidate set (canonical padded rows into
@@ -265,7 +288,7 @@ cudaError_t launch_partition_out(int d, const gres_plan_cfg &cfg, int64_t n, Wor
                                  uint32_t *d_order, uint32_t *d_tile_min, cudaStream_t st);
 // The grid-dominance kernel for one query; *counter must be 0.
 cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,
-                             unsigned long long *tests, cudaStream_t st);
+                             unsigned long long *tests, cudaStream_t st, const PartCount &pc = PartCount());
 // One launch for up to 256 queries of the same d; *counter must be 0.
 cudaError_t launch_dominance_batch(int d, int slots, const DomQuery *qs, int count, unsigned *counter,
                                    cudaStream_t st);

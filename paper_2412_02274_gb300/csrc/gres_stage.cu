@@ -39,6 +39,7 @@
 // shared memory with cp.async when they fit (they do for skylines up to
 // about 6,900 rows at d = 6), otherwise read through L1.
 #include "cluster.cuh"
+#include "radix.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -112,9 +113,9 @@ cudaError_t upload_steps(const uint32_t *h_steps, int k, uint32_t *steps, uint32
         k_upload_steps<kRawSmall><<<1, 256, 0, st>>>(c, steps, magic, h, n, zero, gbits, sel); note_launch();
         return cudaGetLastError();
     }
-    static RawSteps<kRawLarge> c;   // 32 KB: not on the stack
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
+    // 32 KB: not on the stack; one per host thread, so concurrent callers do not wait
+    // for each other (launch arguments are copied when the launch is queued)
+    thread_local RawSteps<kRawLarge> c;
     for (int off = 0; off < k; off += kRawLarge) {
         c.off = off;
         c.count = std::min(kRawLarge, k - off);
@@ -162,11 +163,6 @@ __device__ __forceinline__ void ldg_row(const uint32_t *base, long long r, uint3
     }
 }
 
-__global__ void k_reset_keyrange(WsHeader *h) {
-    h->key_min = ~0ull;
-    h->key_max = 0ull;
-}
-
 struct PartArgs {
     int scheme;      // gres_part
     int m;           // GRID / ANGULAR slices
@@ -177,23 +173,6 @@ struct PartArgs {
     int key32;       // every key fits 32 bits (the sort can stay in shared memory)
     unsigned long long thr[64];   // ANGULAR: tan^2(j pi / 2m) * 2^32, j = 1 .. m-1
 };
-
-// Warp-reduced atomic min/max of the sort-key range; lanes without an item
-// pass valid = false.
-__device__ __forceinline__ void key_minmax(unsigned long long k, bool valid, WsHeader *h) {
-    unsigned long long kmin = valid ? k : ~0ull, kmax = valid ? k : 0ull;
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long a = __shfl_xor_sync(kFull, kmin, o);
-        unsigned long long b = __shfl_xor_sync(kFull, kmax, o);
-        kmin = a < kmin ? a : kmin;
-        kmax = b > kmax ? b : kmax;
-    }
-    if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
-        atomicMin(&h->key_min, kmin);
-        atomicMax(&h->key_max, kmax);
-    }
-}
 
 template <int D>
 __device__ __forceinline__ uint32_t pick(const uint32_t (&x)[D], int q) {
@@ -294,53 +273,6 @@ __device__ __forceinline__ unsigned long long sliced_key(const uint32_t *sky_row
     return (slice << a.obits) | morton_range<D>(x, h, a.bpa);
 }
 
-template <int D>
-__global__ void k_part_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
-                            unsigned long long *keys, uint32_t *vals) {
-    const long long S = h->n_sky;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long start = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    // every lane of a warp takes part in key_minmax: loop to a warp-uniform bound
-    const long long lim = ((S + 31) / 32) * 32;
-    for (long long j = start; j < lim; j += stride) {
-        unsigned long long key = 0;
-        const bool valid = j < S;
-        if (valid) {
-            key = part_key<D>(sky_rows, j, h, a);
-            keys[j] = key;
-            vals[j] = (uint32_t)j;
-        }
-        key_minmax(key, valid, h);
-    }
-}
-
-// SLICED second pass (after k_reset_keyrange): the row of rank r in the
-// order of x_dim falls in slice floor(r p / S) (Sec. 3.1); the new key orders
-// rows by (slice, morton16). Reads the sorted buffer, writes buffer 0 at the same
-// index (in place when the sorted buffer is buffer 0).
-template <int D>
-__global__ void k_sliced_keys(const uint32_t *sky_rows, WsHeader *h, PartArgs a,
-                              unsigned long long *keys0, uint32_t *vals0, const uint32_t *vals1) {
-    const long long S = h->n_sky;
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long lim = ((S + 31) / 32) * 32;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < lim; r += stride) {
-        unsigned long long key = 0;
-        uint32_t j = 0;
-        const bool valid = r < S;
-        if (valid) {
-            j = vals[r];
-            key = sliced_key<D>(sky_rows, j, r, S, h, a);
-        }
-        if (valid) {
-            keys0[r] = key;
-            vals0[r] = j;
-        }
-        key_minmax(key, valid, h);
-    }
-}
-
 // Candidate rows in partition order, padded to whole 32-row tiles with
 // sentinel rows (all ones: never dominate), each tile's per-attribute minimum
 // (tmin) and each 1024-row super-tile's minimum (smin). One block of 1024
@@ -396,25 +328,109 @@ __device__ __forceinline__ void permute_super(const uint32_t *sky_rows, const ui
     __syncthreads();
 }
 
+// The partitioning of a skyline of more than kClusterSortMax rows, as one
+// cooperative launch: the partition keys (partition number << obits | order
+// inside the partition), the stable radix sort (for SLICED: by the chosen
+// attribute, then by (slice, order) with slice floor(rank p / S), Sec. 3.1),
+// then the candidate layout -- rows in that order in 32-row tiles padded with
+// sentinel rows, tile and super-tile minima, perm (partition position ->
+// skyline position). Returns at once (every block) for at most
+// kClusterSortMax skyline rows: k_part_cluster partitions those. The key range
+// was cleared by k_compact_sky.
 template <int D>
-__global__ void __launch_bounds__(1024)
-k_permute(const uint32_t *sky_rows, const uint32_t *vals0, const uint32_t *vals1,
-          const WsHeader *h, int identity, uint32_t *cand, uint32_t *tmin, uint32_t *smin,
-          uint32_t *perm) {
+__global__ void __launch_bounds__(kRxThreads)
+k_part_coop(const uint32_t *sky_rows, Workspace ws, PartArgs a, int passes1, int passes2) {
     constexpr int DP = padded_dims(D);
+    __shared__ RadixShared s;
+    WsHeader *h = ws.hdr;
     const long long S = h->n_sky;
+    if (S <= kClusterSortMax) return;
+    const long long stride = (long long)gridDim.x * kRxThreads;
+    const long long gt = (long long)blockIdx.x * kRxThreads + threadIdx.x;
+    const bool none = a.scheme == GRES_PART_NONE;
+    int sel = 0;
+    if (!none) {
+        unsigned long long kmn = ~0ull, kmx = 0ull;
+        for (long long j = gt; j < S; j += stride) {
+            const unsigned long long key = part_key<D>(sky_rows, j, h, a);
+            ws.keys[0][j] = key;
+            ws.vals[0][j] = (uint32_t)j;
+            kmn = key < kmn ? key : kmn;
+            kmx = key > kmx ? key : kmx;
+        }
+        rx_key_range(kmn, kmx, h);
+        if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
+        sel = rx_sort_coop(ws, S, passes1, s);
+        if (sel < 0) return;
+        if (a.scheme == GRES_PART_SLICED) {
+            // rank r -> slice floor(r p / S); the new keys order rows by (slice, order)
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                h->key_min = ~0ull;
+                h->key_max = 0ull;
+            }
+            if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
+            const uint32_t *vs = ws.vals[sel];
+            kmn = ~0ull;
+            kmx = 0ull;
+            for (long long r = gt; r < S; r += stride) {
+                const uint32_t j = vs[r];
+                const unsigned long long key = sliced_key<D>(sky_rows, j, r, S, h, a);
+                ws.keys[0][r] = key;   // in place when the sorted buffer is buffer 0
+                ws.vals[0][r] = j;
+                kmn = key < kmn ? key : kmn;
+                kmx = key > kmx ? key : kmx;
+            }
+            rx_key_range(kmn, kmx, h);
+            if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
+            sel = rx_sort_coop(ws, S, passes2, s);
+            if (sel < 0) return;
+        }
+    }
+    // candidate layout: one warp per tile
+    const uint32_t *vals = ws.vals[sel];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long T = (S + kTileRows - 1) / kTileRows;
+    for (long long tile = (long long)blockIdx.x * kRxWarps + w; tile < T; tile += (long long)gridDim.x * kRxWarps) {
+        const long long i = tile * kTileRows + lane;
+        uint32_t x[DP];
+        if (i < S) {
+            const uint32_t j = none ? (uint32_t)i : vals[i];
+            ws.perm[i] = j;
+            const uint4 *p = reinterpret_cast<const uint4 *>(sky_rows + (long long)j * DP);
+            const uint4 a0 = p[0];
+            x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+            if (DP == 8) { const uint4 b = p[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
+        } else {
+            #pragma unroll
+            for (int q = 0; q < DP; q++) x[q] = kSentinel;
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(ws.cand + i * DP);
+        dst[0] = make_uint4(x[0], x[1], x[2], x[3]);
+        if (DP == 8) dst[1] = make_uint4(x[4 % DP], x[5 % DP], x[6 % DP], x[7 % DP]);
+        #pragma unroll
+        for (int q = 0; q < DP; q++) {
+            uint32_t m = x[q];
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(kFull, m, o));
+            if (lane == 0) ws.tmin[tile * DP + q] = m;
+        }
+    }
+    if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
     const long long T2 = (T + 31) / 32;
-    if ((long long)blockIdx.x >= T2) return;
-    __shared__ uint32_t wm[32][DP];
-    permute_super<D>(sky_rows, h->sorted_sel ? vals1 : vals0, identity, S, (long long)blockIdx.x, cand, tmin,
-                     smin, perm, wm);
+    for (long long k = gt; k < T2 * DP; k += stride) {
+        const long long sup = k / DP;
+        const int q = (int)(k % DP);
+        uint32_t m = kSentinel;
+        for (long long t = sup * 32; t < min(T, sup * 32 + 32); t++) m = min(m, ws.tmin[t * DP + q]);
+        ws.smin[sup * DP + q] = m;
+    }
 }
 
-// The whole partitioning of a skyline of S rows as one cluster launch: keys,
-// the stable sort (two for SLICED: by the chosen attribute, then by slice and
-// Morton code), and the candidate layout -- what k_part_keys, the radix sorts,
-// k_sliced_keys and k_permute compute.
+// The whole partitioning of a skyline of at most kClusterSortMax rows as one
+// cluster launch: keys, the stable sort (two for SLICED: by the chosen
+// attribute, then by slice and Morton code), and the candidate layout -- what
+// the cooperative partition kernel (k_part_coop) computes for larger skylines.
+// Returns at once (every CTA) for a larger skyline.
 template <int D>
 __global__ void __launch_bounds__(kClThreads)
 k_part_cluster(const uint32_t *sky_rows, WsHeader *h, PartArgs a, unsigned long long *k0, uint32_t *v0,
@@ -428,6 +444,7 @@ k_part_cluster(const uint32_t *sky_rows, WsHeader *h, PartArgs a, unsigned long 
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const long long tt = (long long)C * kClThreads, gt = (long long)r * kClThreads + threadIdx.x;
     const long long S = h->n_sky;
+    if (S > kClusterSortMax) return;   // k_part_coop partitions it (every CTA returns here)
     const bool none = a.scheme == GRES_PART_NONE;
     int sel = 0;
     if (!none && a.key32) {
@@ -583,9 +600,25 @@ __global__ void k_partition_out(const WsHeader *h, const unsigned long long *key
     }
 }
 
+// Partition number per partition position (GRES_FLAG_COUNT_PARTS): the high
+// bits of the final sort key (the cluster path's keys when S <= kClusterSortMax,
+// with obits_small order bits, the cooperative path's above, with obits_large);
+// 0 without partitioning; ~0 for the padding rows of the last tile.
+__global__ void k_part_ids(const WsHeader *h, const unsigned long long *keys0, const unsigned long long *keys1,
+                           int none, int obits_small, int obits_large, uint32_t *pid) {
+    const long long S = h->n_sky;
+    const long long lim = (S + kTileRows - 1) / kTileRows * kTileRows;
+    const unsigned long long *keys = h->sorted_sel ? keys1 : keys0;
+    const int obits = S <= kClusterSortMax ? obits_small : obits_large;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < lim;
+         i += (long long)gridDim.x * blockDim.x)
+        pid[i] = i >= S ? 0xFFFFFFFFu : none ? 0u : (uint32_t)(keys[i] >> obits);
+}
+
 // ---- the pairwise grid-dominance kernel ------------------------------------
 struct DomArgs {
     DomQuery q;
+    PartCount pc;
     unsigned *counter;        // work counter (zeroed before the launch)
     unsigned long long *tests;
     int smem_words;           // dynamic shared memory, in words
@@ -596,41 +629,16 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 
-// Threads per block of the grid-dominance kernels (one block per SM): as many
-// warps as the per-thread registers of each (D, SLOTS) leave room for. Each
-// of the SM's four sub-partitions holds 16,384 registers and a quarter of the
-// warps, so w warps per sub-partition allow 512 / w registers per thread
-// (rounded down to a multiple of 8): 3 -> 168, 4 -> 128, 5 -> 96, 6 -> 80, 7 -> 72.
-// packed_bounds: the kernels (single query / batch) and (D, SLOTS) for which
-// the packed cell bounds raise the warp count or avoid register spills; the
-// others keep both corners (a few instructions less per test).
-template <int D, int SLOTS, bool BATCH>
-__host__ __device__ constexpr bool packed_bounds() {
-    return BATCH ? !(D == 1 || (SLOTS == 4 && D == 6))
-                 : !(D == 1 || D == 6 || (SLOTS == 8 && D == 4));
-}
-
+// Threads per block of the grid-dominance kernels (one block per SM). A target's
+// search is one long chain of dependent warp operations, so the kernels run as
+// many warps per SM as the registers allow: the cell bounds of a target are
+// made on the fly for each slot test instead of being kept in registers.
 template <int D, int SLOTS, bool GM = false>
 __host__ __device__ constexpr int dom_threads() {
-    return GM ? (SLOTS == 8 ? (D <= 2 ? 640 : D <= 4 ? 512 : D <= 6 ? 384 : 256)
-                            : (D <= 1 ? 896 : D <= 2 ? 768 : D <= 4 ? 640 : D <= 6 ? 512 : 384))
-              : (SLOTS == 8 ? (D <= 1 ? 768 : D <= 3 ? 640 : D <= 5 ? 512 : 384)
-                            : (D <= 2 ? 896 : D <= 3 ? 768 : D <= 5 ? 640 : 512));
+    return GM ? 768 : 1024;
 }
 
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
-
-// Canonical cell [lo, hi] of a target at one width from its stored corner x:
-// the raw cell is [lv, lv + e] with e = min(delta - 1, 2^32 - 1 - lv) (the
-// top cell is cut at 2^32 - 1); canonically that is [lv, lv + e] for
-// smaller-is-better (x = lv, 2^32 - 1 - lv = ~x) and [~lv - e, ~lv] for
-// larger-is-better (x = ~lv, 2^32 - 1 - lv = x). A zero corner with dir 0 or 1
-// gives lo = 0, so nothing is strictly below it (lanes past K).
-__device__ __forceinline__ void cell_bounds(uint32_t x, uint32_t dm1, int dir, uint32_t &lo, uint32_t &hi) {
-    const uint32_t e = min(dm1, dir ? x : ~x);
-    lo = dir ? x - e : x;
-    hi = dir ? x : x + e;
-}
 
 // Raw cell [lv, uv] of raw value v at one step (mg = the step's division
 // constants and divisor). Widths: [floor(v / w) w, + w - 1] cut at 2^32 - 1.
@@ -705,10 +713,11 @@ k_rep_bound(const uint32_t *cand, const uint32_t *greps, const long long *n_sky,
 // Grid resistance of the target at partition position i of query q (one
 // warp; every lane returns it): the first step at which some candidate's
 // projection dominates the target's projection, else K.
-template <int D, int SLOTS, bool RES, bool PK, bool GM>
+template <int D, int SLOTS, bool RES, bool GM>
 __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
                                            const uint32_t *smin, long long T, unsigned i, uint32_t *wsteps,
-                                           unsigned long long &n_tests, unsigned long long &n_checks) {
+                                           unsigned long long &n_tests, unsigned long long &n_checks,
+                                           const PartCount &pc) {
     constexpr int WS = 32 * SLOTS;
     const int lane = threadIdx.x & 31;
     const int K = qy.K;
@@ -717,20 +726,13 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
     int result = K;
     for (int w0 = 0; w0 < K; w0 += WS) {
         const int wcount = min(WS, K - w0);
-        // this window's widths in shared memory; bounds are made on first use
+        // this window's widths in shared memory
         #pragma unroll
         for (int j = 0; j < SLOTS; j++) {
             const int k = w0 + 32 * j + lane;
             wsteps[32 * j + lane] = k < K ? __ldg(qy.steps + k) : 0xFFFFFFFFu;
         }
         __syncwarp();
-        // Cell of the target at the slot's width, in canonical values. Unpacked: both
-        // corners per attribute (X high, Y low). Packed (fewer registers, so more
-        // warps per SM where that matters): one corner per attribute, X = the low
-        // corner (smaller-is-better) or the high corner (larger-is-better), plus
-        // the width minus one per slot; see cell_bounds.
-        uint32_t X[SLOTS][D], Y[PK ? 1 : SLOTS][PK ? 1 : D], dm1[PK ? SLOTS : 1];
-        unsigned ready = 0;   // slots whose bounds are made
         int best = wcount;
         if (qy.ub) {
             // a known exit step (GRES_FLAG_GRES_REPS): only earlier steps are searched
@@ -744,16 +746,17 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
         uint32_t wl = best > 0 ? wsteps[best - 1] : 0u, wlq = min(wl >> qshift, 0x7FFFFFFu);
         // lane j < SLOTS - 1 holds the widest width of slot j (for the first slot that can matter)
         const uint32_t slot_top = (lane < SLOTS - 1 && 32 * lane + 31 < wcount) ? wsteps[32 * lane + 31] : 0xFFFFFFFFu;
-        // Best-first over three levels -- 1024-row super-tiles, 32-row tiles, rows --
+        // Best-first over two levels -- 1024-row super-tiles, then 32-row tiles --
         // each visited in ascending order of its lower bound on the excess
-        // max_i (s_i - t_i)^+ (keys hold it >> qshift, 27 bits; exact tests below).
+        // max_i (s_i - t_i)^+ (keys hold it >> qshift, 27 bits; exact tests below),
+        // then the rows of a tile whose excess is below delta[best - 1].
         // Anything whose bound reaches delta[best - 1] is skipped.
         const long long T2 = (T + 31) / 32;
-        for (long long sc = 0; sc < T2 && best > 0; sc += 32) {
+        for (long long s0 = 0; s0 < T2 && best > 0; s0 += 32) {
             uint32_t skey = kNoTile, sex = 0xFFFFFFFFu;
-            if (sc + lane < T2) {
+            if (s0 + lane < T2) {
                 uint32_t mn[D];
-                if (RES) ld_row<D>(smin, sc + lane, mn); else ldg_row<D>(smin, sc + lane, mn);
+                if (RES) ld_row<D>(smin, s0 + lane, mn); else ldg_row<D>(smin, s0 + lane, mn);
                 uint32_t emax = 0;
                 bool can = false;
                 #pragma unroll
@@ -774,7 +777,7 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                 const int sl = (int)(mk & 31u);
                 if (lane == sl) skey = kNoTile;
                 if (__shfl_sync(kFull, sex, sl) >= wl) continue;
-                const long long sup = sc + sl;
+                const long long sup = s0 + sl;
                 // tile level inside the super-tile: lane = tile
                 uint32_t tkey = kNoTile, tex = 0xFFFFFFFFu;
                 const long long tile = sup * 32 + lane;
@@ -802,78 +805,65 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                     if (lane == tl) tkey = kNoTile;
                     if (__shfl_sync(kFull, tex, tl) >= wl) continue;
                     const long long r0 = (sup * 32 + tl) * kTileRows;
-                    // candidate level: lane r looks at row r of the tile
-                    uint32_t s[D];
-                    if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
+                    // row level: lane r looks at row r of the tile; a row can dominate t
+                    // only at widths wider than its excess e_r, and it matters only if
+                    // such a width comes before best
                     uint32_t e_r = 0;
                     bool can_r = false;
-                    #pragma unroll
-                    for (int q = 0; q < D; q++) {
-                        e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
-                        can_r |= s[q] < t[q];
+                    {
+                        uint32_t s[D];
+                        if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
+                        #pragma unroll
+                        for (int q = 0; q < D; q++) {
+                            e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
+                            can_r |= s[q] < t[q];
+                        }
                     }
                     n_checks += 32;
-                    // a row can dominate t only at widths wider than e_r; it matters only if such
-                    // a width comes before best. Rows are taken in ascending order of e_r.
-                    uint32_t ckey = (can_r && e_r < wl) ? ((min(e_r >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane)
-                                                        : 0xFFFFFFFFu;
-                    for (;;) {
-                        const uint32_t ck = __reduce_min_sync(kFull, ckey);
-                        if (ck == 0xFFFFFFFFu) break;
-                        const int c = (int)(ck & 31u);
-                        if (lane == c) ckey = 0xFFFFFFFFu;
-                        const uint32_t ec = __shfl_sync(kFull, e_r, c);
-                        if (ec >= wl) {
-                            if ((ck >> 5) > wlq) break;
-                            continue;
+                    if (pc.pcnt) {
+                        // per-partition split: rows of the target's partition, and the others
+                        const uint32_t pt = __ldg(pc.pid + i);
+                        const unsigned loc = __popc(__ballot_sync(kFull, __ldg(pc.pid + r0 + lane) == pt));
+                        if (lane == 0 && pt < pc.nparts) {
+                            atomicAdd(pc.pcnt + 2 + 4ull * pt + 1, (unsigned long long)loc);
+                            atomicAdd(pc.pcnt + 2 + 4ull * pt + 3, (unsigned long long)(32 - loc));
                         }
-                        uint32_t sc[D];
-                        #pragma unroll
-                        for (int q = 0; q < D; q++) sc[q] = __shfl_sync(kFull, s[q], c);
+                    }
+                    // rows taken in tile order; best only shrinks, so a row is skipped once
+                    // its excess reaches the current delta[best - 1]
+                    unsigned elig = __ballot_sync(kFull, can_r && e_r < wl);
+                    while (elig) {
+                        const int c = __ffs(elig) - 1;
+                        elig &= elig - 1;
+                        const uint32_t ec = __shfl_sync(kFull, e_r, c);
+                        if (ec >= wl) continue;
+                        uint32_t cv[D];   // the row, read by every lane (broadcast)
+                        if (RES) ld_row<D>(cand, r0 + c, cv); else ldg_row<D>(cand, r0 + c, cv);
                         // first slot holding a width wider than ec
                         const int jlo = __popc(__ballot_sync(kFull, slot_top <= ec));
                         const int jhi = (best - 1) >> 5;
-                        #pragma unroll
-                        for (int j = 0; j < SLOTS; j++) {
-                            if (j < jlo || j > jhi) continue;
-                            if (!(ready & (1u << j))) {
-                                ready |= 1u << j;
-                                const int k = w0 + 32 * j + lane;
-                                const bool live = k < K;
-                                const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
-                                                      : make_uint4(1u, 0u, 0u, 1u);
-                                const uint32_t delta = mg.w;
-                                if (PK) dm1[PK ? j : 0] = delta - 1u;
-                                #pragma unroll
-                                for (int q = 0; q < D; q++) {
-                                    const uint32_t v = qy.dir ? ~t[q] : t[q];
-                                    if (PK) {
-                                        // raw cell [lv, lv + min(delta - 1, ~lv)]: canonical low corner lv
-                                        // (MIN) or canonical high corner ~lv (MAX); lanes past K never match
-                                        const uint32_t lv = udiv(v, mg.x, mg.y, mg.z) * delta;
-                                        X[j][q] = live ? (qy.dir ? ~lv : lv) : 0u;
-                                    } else {
-                                        uint32_t lv, uv;
-                                        raw_cell(v, mg, GM ? qy.gbits : 0, lv, uv);
-                                        X[j][q] = live ? (qy.dir ? ~lv : uv) : 0u;
-                                        Y[PK ? 0 : j][PK ? 0 : q] = live ? (qy.dir ? ~uv : lv) : 0u;
-                                    }
-                                }
-                            }
+                        for (int j = jlo; j <= jhi; j++) {
+                            // the target's cell at this lane's width, canonical [lo, hi];
+                            // lanes past K never match
+                            const int k = w0 + 32 * j + lane;
+                            const bool live = k < K;
+                            const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
+                                                  : make_uint4(1u, 0u, 0u, 1u);
                             bool le = true, lt = false;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                uint32_t lo, hi;
-                                if (PK) {
-                                    cell_bounds(X[j][q], dm1[PK ? j : 0], qy.dir, lo, hi);
-                                } else {
-                                    hi = X[j][q];
-                                    lo = Y[PK ? 0 : j][PK ? 0 : q];
-                                }
-                                le &= sc[q] <= hi;
-                                lt |= sc[q] < lo;
+                                uint32_t lv, uv;
+                                raw_cell(qy.dir ? ~t[q] : t[q], mg, GM ? qy.gbits : 0, lv, uv);
+                                const uint32_t hi = live ? (qy.dir ? ~lv : uv) : 0u;
+                                const uint32_t lo = live ? (qy.dir ? ~uv : lv) : 0u;
+                                le &= cv[q] <= hi;
+                                lt |= cv[q] < lo;
                             }
                             n_tests += 32;
+                            if (pc.pcnt && lane == 0 && __ldg(pc.pid + i) < pc.nparts) {
+                                const uint32_t pt = __ldg(pc.pid + i);
+                                atomicAdd(pc.pcnt + 2 + 4ull * pt + (__ldg(pc.pid + r0 + c) == pt ? 0 : 2), 32ull);
+                            }
                             const unsigned msk = __ballot_sync(kFull, le & lt);
                             if (msk) {
                                 best = min(best, 32 * j + __ffs(msk) - 1);
@@ -931,9 +921,8 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            constexpr bool PK = !GM && packed_bounds<D, SLOTS, false>();
-            const int r = dom_target<D, SLOTS, true, PK, GM>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T,
-                                                     i, wsteps, n_tests, n_checks);
+            const int r = dom_target<D, SLOTS, true, GM>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T,
+                                                     i, wsteps, n_tests, n_checks, a.pc);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
     } else {
@@ -942,9 +931,8 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            constexpr bool PK = !GM && packed_bounds<D, SLOTS, false>();
-            const int r = dom_target<D, SLOTS, false, PK, GM>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests,
-                                                      n_checks);
+            const int r = dom_target<D, SLOTS, false, GM>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests,
+                                                      n_checks, a.pc);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
     }
@@ -999,9 +987,8 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
         const long long T = (S + kTileRows - 1) / kTileRows;
         const unsigned local = (unsigned)(g - first[lo]);
         const unsigned i = q.iperm ? __ldg(q.iperm + q.t0 + local) : local;
-        constexpr bool PK = packed_bounds<D, SLOTS, true>();
-        const int r = dom_target<D, SLOTS, false, PK, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
-                                                             n_checks);
+        const int r = dom_target<D, SLOTS, false, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
+                                                             n_checks, PartCount());
         if (lane == 0) q.out[q.iperm ? local : q.perm[i]] = r;
     }
 }
@@ -1094,7 +1081,6 @@ int order_bits(const gres_plan_cfg &cfg, int d, int64_t n, int *pbits, int *bpa)
 
 template <int D>
 cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cudaStream_t st) {
-    const int rb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)g_sm_count);
     const int scheme = cfg.scheme;
     PartArgs pa;
     std::memset(&pa, 0, sizeof(pa));
@@ -1110,40 +1096,36 @@ cudaError_t partition_d(const gres_plan_cfg &cfg, int64_t n, Workspace &ws, cuda
         }
     }
     auto passes = [&](int bits) { return (bits + 7) / 8; };
+    // A skyline of at most kClusterSortMax rows is partitioned in one cluster launch
+    // (16-bit keys), a larger one in one cooperative launch (32-bit keys). S is known on
+    // the device only: for inputs above kClusterSortMax rows both are queued and each
+    // returns at once for the other size.
+    PartArgs ps = pa;
+    int pbits_s = 0;
+    ps.obits = order_bits(cfg, D, std::min<int64_t>(n, kClusterSortMax), &pbits_s, &ps.bpa);
+    ps.key32 = pbits_s + ps.obits <= 32 ? 1 : 0;   // SLICED's first key is one 32-bit value
+    static bool configured = false;
+    cudaError_t e = launch_cluster(k_part_cluster<D>, kClSmemBytes, &configured, st, (const uint32_t *)ws.sky_rows,
+                                   ws.hdr, ps, ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], ws.cand, ws.tmin,
+                                   ws.smin, ws.perm);
+    if (e != cudaSuccess || n <= kClusterSortMax) return e;
     int pbits = 0;
     pa.obits = order_bits(cfg, D, n, &pbits, &pa.bpa);
-    pa.key32 = pbits + pa.obits <= 32 ? 1 : 0;   // SLICED's first key is one 32-bit value
-    cudaError_t e;
-    if (n <= kClusterSortMax) {
-        static bool configured = false;
-        return launch_cluster(k_part_cluster<D>, kClSmemBytes, &configured, st, (const uint32_t *)ws.sky_rows,
-                              ws.hdr, pa, ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], ws.cand, ws.tmin,
-                              ws.smin, ws.perm);
-    }
-    if (scheme != GRES_PART_NONE) {
-        k_part_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0]); note_launch();
-        const int bits1 = scheme == GRES_PART_SLICED ? 32 : pa.obits + pbits;
-        e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(bits1), st);
-        if (e != cudaSuccess) return e;
-        if (scheme == GRES_PART_SLICED) {
-            k_reset_keyrange<<<1, 1, 0, st>>>(ws.hdr); note_launch();
-            k_sliced_keys<D><<<rb, 256, 0, st>>>(ws.sky_rows, ws.hdr, pa, ws.keys[0], ws.vals[0], ws.vals[1]); note_launch();
-            e = launch_radix_sort(ws, n, &ws.hdr->n_sky, passes(pa.obits + pbits), st);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
-    k_permute<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.sky_rows, ws.vals[0], ws.vals[1], ws.hdr,
-                                                  scheme == GRES_PART_NONE ? 1 : 0, ws.cand, ws.tmin, ws.smin,
-                                                  ws.perm); note_launch();
+    pa.key32 = pbits + pa.obits <= 32 ? 1 : 0;
+    static int coop = 0;
+    if (!coop && (e = coop_blocks(k_part_coop<D>, &coop)) != cudaSuccess) return e;
+    e = launch_coop(k_part_coop<D>, coop, st, (const uint32_t *)ws.sky_rows, ws, pa,
+                    passes(scheme == GRES_PART_SLICED ? 32 : pa.obits + pbits), passes(pa.obits + pbits));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t dominance_d(int slots, const DomQuery &q, unsigned *counter, unsigned long long *tests,
-                        cudaStream_t st) {
+                        cudaStream_t st, const PartCount &pc) {
     DomArgs a;
     a.q = q;
+    a.pc = pc;
     a.counter = counter;
     a.tests = tests;
     a.smem_words = 0;
@@ -1230,10 +1212,10 @@ cudaError_t launch_partition_out(int d, const gres_plan_cfg &cfg, int64_t n, Wor
 }
 
 cudaError_t launch_dominance(int d, int slots, const DomQuery &q, unsigned *counter,
-                             unsigned long long *tests, cudaStream_t st) {
+                             unsigned long long *tests, cudaStream_t st, const PartCount &pc) {
     cudaError_t e = device_props();
     if (e != cudaSuccess) return e;
-#define GRES_DOM(D) dominance_d<D>(slots, q, counter, tests, st)
+#define GRES_DOM(D) dominance_d<D>(slots, q, counter, tests, st, pc)
     GRES_DISPATCH_D(d, GRES_DOM)
 #undef GRES_DOM
 }
@@ -1271,6 +1253,16 @@ cudaError_t launch_rep_bound(int d, int64_t n, Workspace &ws, int k, int dir, in
 #undef GRES_RB
 }
 
+int64_t plan_partitions(const gres_plan_cfg &cfg, int d) {
+    if (cfg.scheme == GRES_PART_SLICED) return cfg.p;
+    if (cfg.scheme == GRES_PART_GRID || cfg.scheme == GRES_PART_ANGULAR) {
+        int64_t cells = 1;
+        for (int i = 0; i < (cfg.scheme == GRES_PART_GRID ? d : d - 1); i++) cells *= cfg.m;
+        return cells;
+    }
+    return 1;
+}
+
 cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int dir, int k,
                               const gres_plan_cfg &cfg, Workspace &ws,
                               const int64_t * /*d_sky_idx*/, int32_t *d_step_idx,
@@ -1293,6 +1285,19 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
     q.dir = dir;
     q.gbits = gbits;
     unsigned long long *counts = (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr;
+    PartCount pc;
+    if ((cfg.flags & GRES_FLAG_COUNT_PARTS) && d_tests) {
+        if ((e = device_props()) != cudaSuccess) return e;
+        int pb = 0, bpa = 0;
+        const int ob_s = order_bits(cfg, d, std::min<int64_t>(n, kClusterSortMax), &pb, &bpa);
+        const int ob_l = order_bits(cfg, d, n, &pb, &bpa);
+        const int blocks = (int)std::min<int64_t>((n + kTileRows + 255) / 256, (int64_t)g_sm_count * 4);
+        k_part_ids<<<blocks, 256, 0, st>>>(ws.hdr, ws.keys[0], ws.keys[1], cfg.scheme == GRES_PART_NONE ? 1 : 0,
+                                           ob_s, ob_l, ws.pid); note_launch();
+        pc.pid = ws.pid;
+        pc.pcnt = d_tests;
+        pc.nparts = (unsigned)std::min<int64_t>(plan_partitions(cfg, d), 0xFFFFFFFFll);
+    }
     stage_begin(kStageDominance, st);   // the representative bound pass counts as grid-dominance work
     if (cfg.flags & GRES_FLAG_GRES_REPS) {
         q.ub = ws.res;
@@ -1303,7 +1308,7 @@ cudaError_t launch_gres_stage(const uint32_t * /*d_data*/, int64_t n, int d, int
         }
     }
     e = launch_dominance(d, cfg.slots, q, &ws.hdr->work_next,
-                         (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr, st);
+                         (cfg.flags & GRES_FLAG_COUNT_TESTS) ? d_tests : nullptr, st, pc);
     stage_end(kStageDominance, st);
     return e;
 }

@@ -9,7 +9,11 @@
 // cell moves every iteration, so no comparison can be hoisted out of the
 // loop; the move costs 2d adds per kProbeCands tests. Operands never leave
 // registers: the rate is bounded by the integer pipes alone.
-#include "gres_internal.cuh"
+//
+// It also holds the check of the cooperative sorts' bounded grid-wide wait
+// (gres_barrier_probe): one block stays away from the barrier on purpose, and
+// the others must give up, flag the timeout and return.
+#include "radix.cuh"
 
 namespace gres {
 
@@ -78,6 +82,14 @@ cudaError_t launch_d(int iters, int blocks, unsigned long long *sink, cudaStream
     return cudaGetLastError();
 }
 
+// Every block but `absent` waits at one grid-wide barrier (words: arrivals,
+// generation, status). With absent in [0, gridDim.x) the waits run out.
+__global__ void __launch_bounds__(kRxThreads) k_barrier_probe(unsigned *words, int absent) {
+    __shared__ int ok;
+    if ((int)blockIdx.x == absent) return;
+    grid_barrier(words, words + 2, &ok);
+}
+
 }  // namespace
 
 cudaError_t launch_test_peak(int d, int iters, int blocks, unsigned long long *sink, cudaStream_t st,
@@ -95,3 +107,18 @@ cudaError_t launch_test_peak(int d, int iters, int blocks, unsigned long long *s
 }
 
 }  // namespace gres
+
+extern "C" gres_status gres_barrier_probe(int32_t absent, unsigned *d_words, void *stream, uint32_t *h_status) {
+    if (!d_words || !h_status) return gres::set_error(GRES_EINVAL, "d_words / h_status is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_words, 0, 3 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = gres::launch_coop(gres::k_barrier_probe, sms, st, d_words, (int)absent);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_status, d_words + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return gres::set_error(GRES_ECUDA, cudaGetErrorString(e));
+    if (*h_status & gres::kStatusTimeout) return gres::set_error(GRES_ETIMEOUT, "a grid-wide wait ran out");
+    return GRES_OK;
+}

@@ -12,7 +12,10 @@
 //               their rows so that runs of 32 are spatially tight.
 //               Representatives dominated by another one stay: by
 //               transitivity the filter drops the same rows either way.
-//   3. filter:  every row, in input order, against the representatives.
+//   3. filter:  a first pass, one row per thread, against 32 of the
+//               representatives (one per spatial run: the one dominating the
+//               largest part of the data's box); then every row it leaves
+//               against all the representatives.
 //   4. group:   the survivors in a spatial order (a Morton code over their
 //               bounding box: 16 bits, or at least 4 bits per attribute when
 //               more than 131,072 rows survive) in 32-row tiles with
@@ -24,6 +27,7 @@
 //   6. flags by original row -> ascending row numbers, plus the canonical
 //      skyline rows for the gres stage.
 #include "cluster.cuh"
+#include "radix.cuh"
 
 #include <algorithm>
 
@@ -131,20 +135,6 @@ __global__ void k_init(WsHeader *h, long long n, uint32_t *sel) {
     clear_sel_hist(sel);
 }
 
-__device__ __forceinline__ void warp_minmax_atomic(unsigned long long kmin, unsigned long long kmax,
-                                                   WsHeader *h) {
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, o);
-        unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, o);
-        kmin = a < kmin ? a : kmin;
-        kmax = b > kmax ? b : kmax;
-    }
-    if ((threadIdx.x & 31) == 0 && kmin <= kmax) {
-        atomicMin(&h->key_min, kmin);
-        atomicMax(&h->key_max, kmax);
-    }
-}
 
 // ---- representative selection ------------------------------------------------
 // The representatives are the rows of smallest f (at most R of them, Sec. 3.1),
@@ -210,21 +200,45 @@ template <int D>
 __global__ void __launch_bounds__(1024)
 k_keys(const uint32_t *data, long long n, int dir, unsigned long long *keys, WsHeader *h, uint32_t *hist, int R) {
     __shared__ uint32_t sh[kSelBuckets];
+    __shared__ uint32_t blo[D], bhi[D];
     for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) sh[b] = 0;
+    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
     __syncthreads();
+    uint32_t lo[D], hi[D];
+    #pragma unroll
+    for (int j = 0; j < D; j++) { lo[j] = 0xFFFFFFFFu; hi[j] = 0u; }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         uint32_t x[D];
         load_canon<D>(data, i, dir, x);
         unsigned long long k = 0;
         #pragma unroll
-        for (int j = 0; j < D; j++) k += x[j];
+        for (int j = 0; j < D; j++) {
+            k += x[j];
+            lo[j] = min(lo[j], x[j]);
+            hi[j] = max(hi[j], x[j]);
+        }
         keys[i] = k;
         atomicAdd(&sh[fbucket(k)], 1u);
+    }
+    // the data's per-attribute range (dlo / dhi: the first filter pass ranks its
+    // representatives by the part of that box they dominate)
+    #pragma unroll
+    for (int j = 0; j < D; j++) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[j] = min(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
+            hi[j] = max(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
+        }
+        if ((threadIdx.x & 31) == 0 && lo[j] <= hi[j]) { atomicMin(&blo[j], lo[j]); atomicMax(&bhi[j], hi[j]); }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
         if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    if (threadIdx.x < D && blo[threadIdx.x] <= bhi[threadIdx.x]) {
+        atomicMin(&h->dlo[threadIdx.x], blo[threadIdx.x]);
+        atomicMax(&h->dhi[threadIdx.x], bhi[threadIdx.x]);
+    }
     if (last_block_done(&h->done[0])) {
         const unsigned long long found = sel_find(hist, 0u, R);
         if (threadIdx.x == 0) {
@@ -274,8 +288,8 @@ __device__ __forceinline__ unsigned long long block_bitonic(unsigned long long v
 template <int D>
 __device__ __forceinline__ void rep_sort_block(const uint32_t *data, int dir, const uint32_t *rep_idx, int nc,
                                                WsHeader *h, uint32_t *rows, uint32_t *blocksum, long long nb,
-                                               uint32_t *greps, unsigned long long *sk, uint32_t *xs,
-                                               uint32_t *lo, uint32_t *hi) {
+                                               uint32_t *greps, uint32_t *kill, unsigned long long *sk,
+                                               uint32_t *xs, uint32_t *lo, uint32_t *hi) {
     const int tid = threadIdx.x;
     for (long long j = tid; j < nb; j += kMaxReps) blocksum[j] = 0u;
     if (tid < D) { lo[tid] = 0xFFFFFFFFu; hi[tid] = 0u; }
@@ -283,6 +297,10 @@ __device__ __forceinline__ void rep_sort_block(const uint32_t *data, int dir, co
     uint32_t x[D];
     const uint32_t idx = tid < nc ? __ldcg(rep_idx + tid) : 0xFFFFFFFFu;
     if (tid < nc) load_canon<D>(data, idx, dir, x);
+    else {
+        #pragma unroll
+        for (int q = 0; q < D; q++) x[q] = 0u;
+    }
     #pragma unroll
     for (int q = 0; q < D; q++) {
         xs[q * kMaxReps + tid] = tid < nc ? x[q] : 0u;
@@ -329,6 +347,40 @@ __device__ __forceinline__ void rep_sort_block(const uint32_t *data, int dir, co
         for (int q = 0; q < D; q++) x[q] = xs[q * kMaxReps + c];
         store_row<D>(rows, tid, x);
     }
+    {
+        // The first filter pass's representatives: one per run of 32 in this spatial
+        // order (kKillers = 32 runs at most), the one whose dominated region covers
+        // the largest part of the data's box (score: the sum of log2(dhi_q - x_q + 1),
+        // the log of the box volume above x; ties to the first). Spread over the runs,
+        // they cover different parts of the data. A speed-only choice: correctness
+        // never depends on it. Sentinel rows stand in for missing runs.
+        static_assert(kKillers == kMaxReps / 32, "one first-pass representative per run");
+        constexpr int DP = padded_dims(D);
+        const int lane = tid & 31, w = tid >> 5;
+        unsigned long long key = 0;
+        if (tid < nc) {
+            float sc = 0.f;
+            #pragma unroll
+            for (int q = 0; q < D; q++) sc += __log2f((float)(h->dhi[q] - min(x[q], h->dhi[q])) + 1.f);
+            key = (1ull << 63) | ((unsigned long long)__float_as_uint(sc) << 32) | (unsigned)(31 - lane);
+        }
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            key = other > key ? other : key;
+        }
+        const int src = 31 - (int)(key & 31ull);
+        uint32_t y[D];
+        #pragma unroll
+        for (int q = 0; q < D; q++) y[q] = __shfl_sync(0xffffffffu, x[q], src);
+        if (lane == 0) {
+            if (key) store_row<D>(kill, w, y);
+            else {
+                #pragma unroll
+                for (int q = 0; q < DP; q++) kill[w * DP + q] = kSentinel;
+            }
+        }
+    }
     if (tid == 0) {
         h->n_cand = nc;
         h->n_reps = nc;
@@ -344,7 +396,7 @@ template <int D>
 __global__ void __launch_bounds__(kMaxReps)
 k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *hist, int R,
          unsigned long long *bnd, uint32_t *rep_idx, const uint32_t *data, int dir, uint32_t *rows,
-         uint32_t *blocksum, long long nb, uint32_t *greps) {
+         uint32_t *blocksum, long long nb, uint32_t *greps, uint32_t *kill) {
     // the level-2 histogram, and in the last block the representative sort's arrays
     constexpr size_t kHistBytes = sizeof(uint32_t) * kSelBuckets;
     constexpr size_t kRepBytes = sizeof(unsigned long long) * kMaxReps + sizeof(uint32_t) * (D * kMaxReps + 2 * D);
@@ -393,32 +445,87 @@ k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *his
     __syncthreads();
     unsigned long long *sk = reinterpret_cast<unsigned long long *>(raw);
     uint32_t *xs = reinterpret_cast<uint32_t *>(raw + sizeof(unsigned long long) * kMaxReps);
-    rep_sort_block<D>(data, dir, rep_idx, (int)min(nc_s, (unsigned)kMaxReps), h, rows, blocksum, nb, greps, sk,
-                      xs, xs + D * kMaxReps, xs + D * kMaxReps + D);
+    rep_sort_block<D>(data, dir, rep_idx, (int)min(nc_s, (unsigned)kMaxReps), h, rows, blocksum, nb, greps, kill,
+                      sk, xs, xs + D * kMaxReps, xs + D * kMaxReps + D);
 }
 
-// Survivor flags (not dominated by any representative), rows in input order,
-// plus per-segment survivor counts (kCB-row segments) for the compaction. The
+// First filter pass, one row per thread: every row against the kKillers
+// representatives that dominate the largest part of the data's box. A row one
+// of them dominates is not a skyline tuple (Def. 1): its flag is set to 0.
+// The other rows go, in no particular order, to the list that the warp filter
+// (k_filter) works through. On uniform data this drops most rows for a few
+// compares each; on anticorrelated data it drops few and adds a few percent
+// to the filter's cost.
+constexpr int kPreThreads = 256;
+template <int D>
+__global__ void __launch_bounds__(kPreThreads)
+k_prefilter(const uint32_t *data, int dir, long long n, const uint32_t *kill, WsHeader *h, uint32_t *flags,
+            uint32_t *alive) {
+    constexpr int DP = padded_dims(D);
+    __shared__ uint4 ks[kKillers * DP / 4];
+    for (int j = threadIdx.x; j < kKillers * DP / 4; j += blockDim.x) ks[j] = reinterpret_cast<const uint4 *>(kill)[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool valid = i < n;
+        uint32_t x[D];
+        if (valid) load_canon<D>(data, i, dir, x);
+        else {
+            #pragma unroll
+            for (int q = 0; q < D; q++) x[q] = 0u;
+        }
+        bool live = valid;
+        for (int k = 0; k < kKillers; k++) {
+            if (!__any_sync(0xffffffffu, live)) break;
+            uint32_t sv[D];
+            const uint4 a = ks[k * (DP / 4)];
+            sv[0] = a.x;
+            if (D > 1) sv[1 < D ? 1 : 0] = a.y;
+            if (D > 2) sv[2 < D ? 2 : 0] = a.z;
+            if (D > 3) sv[3 < D ? 3 : 0] = a.w;
+            if (DP == 8) {
+                const uint4 b = ks[k * (DP / 4) + (DP == 8 ? 1 : 0)];
+                if (D > 4) sv[4 < D ? 4 : 0] = b.x;
+                if (D > 5) sv[5 < D ? 5 : 0] = b.y;
+                if (D > 6) sv[6 < D ? 6 : 0] = b.z;
+                if (D > 7) sv[7 < D ? 7 : 0] = b.w;
+            }
+            live = live && !dominates<D>(sv, x);
+        }
+        if (valid && !live) flags[i] = 0u;
+        const unsigned m = __ballot_sync(0xffffffffu, live);
+        unsigned pos = 0;
+        if (lane == 0 && m) pos = atomicAdd(&h->n_alive, (unsigned)__popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (live) alive[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+}
+
+// Survivor flags (not dominated by any representative) of the rows the first
+// pass left (alive, h->n_alive of them, in any order), plus per-segment
+// survivor counts (kCB-row segments of the input) for the compaction. The
 // representatives sit in shared memory (attribute-major) in runs of 32 with
 // each run's per-attribute minimum; a run can hold a dominator of x only if
 // its minimum is <= x in every attribute. Each lane keeps the minimum of run
 // `lane` in registers. A warp takes kFilterRowsPerWarp rows and checks them
 // one at a time: the lanes test the run minima, then the rows of each
 // possible run, stopping at the first dominator. Blocks stay resident and
-// step through kFilterChunk-row chunks, so the representatives are staged
-// once per block and short per-warp chains keep many warps in flight.
+// step through kFilterChunk-row chunks of the list, so the representatives
+// are staged once per block and short per-warp chains keep many warps in
+// flight.
 constexpr int kFilterThreads = 512;
 constexpr int kFilterRowsPerWarp = 4;
 constexpr int kFilterChunk = (kFilterThreads / 32) * kFilterRowsPerWarp;
-static_assert(kCB % kFilterChunk == 0, "a chunk lies inside one compaction segment");
 template <int D>
 __global__ void __launch_bounds__(kFilterThreads)
-k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHeader *h,
+k_filter(const uint32_t *data, int dir, const uint32_t *alive, const uint32_t *reps, WsHeader *h,
          uint32_t *flags, uint32_t *blocksum, long long nb) {
     __shared__ uint32_t rs[D * kMaxReps];
     __shared__ uint32_t rmin[D * (kMaxReps / 32)];
     const int nr = (int)h->n_reps;
     const int nruns = (nr + 31) / 32;
+    const long long na = h->n_alive;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = threadIdx.x; j < nruns * 32; j += kFilterThreads) {
         uint32_t x[D];
@@ -441,12 +548,13 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
     #pragma unroll
     for (int q = 0; q < D; q++) mn[q] = lane < nruns ? rmin[q * (kMaxReps / 32) + lane] : 0xFFFFFFFFu;
     const bool run_ok = lane < nruns;
-    for (long long c0 = (long long)blockIdx.x * kFilterChunk; c0 < n; c0 += (long long)gridDim.x * kFilterChunk) {
+    for (long long c0 = (long long)blockIdx.x * kFilterChunk; c0 < na; c0 += (long long)gridDim.x * kFilterChunk) {
         const long long g0 = c0 + (long long)warp * kFilterRowsPerWarp;
-        if (g0 >= n) continue;
-        const int lim = (int)min((long long)kFilterRowsPerWarp, n - g0);
+        if (g0 >= na) continue;
+        const int lim = (int)min((long long)kFilterRowsPerWarp, na - g0);
         uint32_t x[D];
-        if (lane < lim) load_canon<D>(data, g0 + lane, dir, x);
+        const uint32_t row = lane < lim ? __ldcg(alive + g0 + lane) : 0u;
+        if (lane < lim) load_canon<D>(data, row, dir, x);
         else {
             #pragma unroll
             for (int q = 0; q < D; q++) x[q] = 0u;
@@ -472,8 +580,11 @@ k_filter(const uint32_t *data, int dir, long long n, const uint32_t *reps, WsHea
             }
             if (!dom) alive_mask |= 1u << l;
         }
-        if (lane < lim) flags[g0 + lane] = (alive_mask >> lane) & 1u;
-        if (lane == 0 && alive_mask) atomicAdd(&blocksum[g0 / kCB], (uint32_t)__popc(alive_mask));
+        if (lane < lim) {
+            const uint32_t f = (alive_mask >> lane) & 1u;
+            flags[row] = f;
+            if (f) atomicAdd(&blocksum[row / kCB], 1u);
+        }
     }
     if (last_block_done(&h->done[2])) {
         // survivors' offsets; the sort-key range is cleared for the survivor sort
@@ -542,87 +653,77 @@ k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, uint
 constexpr int surv_fine_bits(int D) { return 16 / D > 4 ? 16 / D : 4; }
 constexpr int surv_sort_passes(int D) { return (D * surv_fine_bits(D) + 7) / 8; }
 
-// Sort keys of the survivors: a Morton code over their range (see
-// surv_fine_bits). The radix sort runs only the digit passes that the key
-// range needs. Also clears the skyline flags.
+// The survivor sort above kClusterSortMax survivors, as one cooperative launch:
+// the survivors' Morton keys over their range (surv_fine_bits bits per
+// attribute), the stable radix sort (the passes the key range needs), then the
+// survivors in that order in 32-row tiles padded with sentinel rows (all ones:
+// never dominate), with each tile's per-attribute minimum (tmin) and each
+// 1024-row super-tile's minimum (smin); perm gets the original row numbers.
+// Returns at once (every block) when at most kClusterSortMax rows survive:
+// k_surv_cluster sorts those. The key range was cleared by k_filter.
 template <int D>
-__global__ void k_surv_keys(const uint32_t *surv_rows, WsHeader *h, unsigned long long *keys, uint32_t *vals,
-                            uint32_t *skyflag, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        skyflag[i] = 0u;   // cleared for k_final
-    const long long M = h->n_surv;
-    const int bits = M > kClusterSortMax ? surv_fine_bits(D) : 16 / D;
-    const long long lim = ((M + 31) / 32) * 32;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < lim;
-         r += (long long)gridDim.x * blockDim.x) {
-        unsigned long long k = 0;
-        if (r < M) {
-            uint32_t x[D];
-            load_row<D>(surv_rows, r, x);
-            k = morton<D>(x, h->slo, h->shi, bits);
-            keys[r] = k;
-            vals[r] = (uint32_t)r;
-        }
-        warp_minmax_atomic(r < M ? k : ~0ull, r < M ? k : 0ull, h);
-    }
-}
-
-// Survivors in spatial order, padded to whole 32-row tiles with sentinel rows
-// (all ones: never dominate), with each tile's per-attribute minimum (tmin)
-// and each 1024-row super-tile's minimum (smin). One block of 1024 threads per
-// super-tile; warp w builds tile w of it.
-template <int D>
-__global__ void __launch_bounds__(1024)
-k_gather_tiles(const uint32_t *surv_rows, const uint32_t *surv_orig, const uint32_t *vals0,
-               const uint32_t *vals1, const WsHeader *h, uint32_t *out_rows, uint32_t *out_orig,
-               uint32_t *tmin, uint32_t *smin) {
+__global__ void __launch_bounds__(kRxThreads)
+k_surv_sort_coop(Workspace ws) {
     constexpr int DP = padded_dims(D);
+    __shared__ RadixShared s;
+    WsHeader *h = ws.hdr;
     const long long M = h->n_surv;
-    const long long T = (M + kTileRows - 1) / kTileRows;
-    const long long T2 = (T + 31) / 32;
-    if ((long long)blockIdx.x >= T2) return;
-    const uint32_t *vals = h->sorted_sel ? vals1 : vals0;
-    __shared__ uint32_t wm[32][DP];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long tile = (long long)blockIdx.x * 32 + w;
-    const long long r = tile * kTileRows + lane;
-    uint32_t x[DP];
-    if (r < M) {
-        const uint32_t j = vals[r];
-        const uint4 *src = reinterpret_cast<const uint4 *>(surv_rows + (long long)j * DP);
-        uint4 a = src[0];
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        if (DP == 8) { uint4 b = src[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
-        out_orig[r] = surv_orig[j];
-    } else {
-        #pragma unroll
-        for (int q = 0; q < DP; q++) x[q] = kSentinel;
+    if (M <= kClusterSortMax) return;
+    const int bits = surv_fine_bits(D);
+    const long long stride = (long long)gridDim.x * kRxThreads;
+    const long long gt = (long long)blockIdx.x * kRxThreads + threadIdx.x;
+    unsigned long long kmn = ~0ull, kmx = 0ull;
+    for (long long r = gt; r < M; r += stride) {
+        uint32_t x[D];
+        load_row<D>(ws.surv_rows, r, x);
+        const unsigned long long k = morton<D>(x, h->slo, h->shi, bits);
+        ws.keys[0][r] = k;
+        ws.vals[0][r] = (uint32_t)r;
+        kmn = k < kmn ? k : kmn;
+        kmx = k > kmx ? k : kmx;
     }
-    if (tile < T) {
-        uint4 *dst = reinterpret_cast<uint4 *>(out_rows + r * DP);
+    rx_key_range(kmn, kmx, h);
+    if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
+    const int sel = rx_sort_coop(ws, M, surv_sort_passes(D), s);
+    if (sel < 0) return;
+    const uint32_t *vals = ws.vals[sel];
+    // tiles: one warp per tile
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long T = (M + kTileRows - 1) / kTileRows;
+    for (long long tile = (long long)blockIdx.x * kRxWarps + w; tile < T; tile += (long long)gridDim.x * kRxWarps) {
+        const long long r = tile * kTileRows + lane;
+        uint32_t x[DP];
+        if (r < M) {
+            const uint32_t j = vals[r];
+            const uint4 *src = reinterpret_cast<const uint4 *>(ws.surv_rows + (long long)j * DP);
+            const uint4 a = src[0];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            if (DP == 8) { const uint4 b = src[1]; x[4 % DP] = b.x; x[5 % DP] = b.y; x[6 % DP] = b.z; x[7 % DP] = b.w; }
+            ws.perm[r] = ws.surv_orig[j];
+        } else {
+            #pragma unroll
+            for (int q = 0; q < DP; q++) x[q] = kSentinel;
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(ws.cand + r * DP);
         dst[0] = make_uint4(x[0], x[1], x[2], x[3]);
         if (DP == 8) dst[1] = make_uint4(x[4 % DP], x[5 % DP], x[6 % DP], x[7 % DP]);
-    }
-    #pragma unroll
-    for (int q = 0; q < DP; q++) {
-        uint32_t m = x[q];
-        #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) {
-            wm[w][q] = m;
-            if (tile < T) tmin[tile * DP + q] = m;
-        }
-    }
-    __syncthreads();
-    if (w == 0) {
         #pragma unroll
         for (int q = 0; q < DP; q++) {
-            uint32_t m = wm[lane][q];
+            uint32_t m = x[q];
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) smin[blockIdx.x * DP + q] = m;
+            if (lane == 0) ws.tmin[tile * DP + q] = m;
         }
+    }
+    if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
+    // super-tile minima: one thread per super-tile and attribute word
+    const long long T2 = (T + 31) / 32;
+    for (long long k = gt; k < T2 * DP; k += stride) {
+        const long long sup = k / DP;
+        const int q = (int)(k % DP);
+        uint32_t m = kSentinel;
+        for (long long t = sup * 32; t < min(T, sup * 32 + 32); t++) m = min(m, ws.tmin[t * DP + q]);
+        ws.smin[sup * DP + q] = m;
     }
 }
 
@@ -688,43 +789,25 @@ k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const 
     }
 }
 
-__global__ void __launch_bounds__(kCT)
-k_count_flags(const uint32_t *flags, long long n, uint32_t *blocksum, long long nb, WsHeader *h) {
-    uint32_t cnt = 0;
-    const long long b0 = (long long)blockIdx.x * kCB;
-    #pragma unroll
-    for (int r = 0; r < kPer; r++) {
-        const long long p = b0 + r * kCT + threadIdx.x;
-        if (p < n) cnt += flags[p];
-    }
-    uint32_t tot;
-    block_scan(cnt, &tot);
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
-    if (last_block_done(&h->done[3])) {
-        const uint32_t total = block_scan_inplace(blocksum, nb);
-        if (threadIdx.x == 0) h->n_sky = total;
-    }
-}
-
 // Skyline rows in ascending row order: row numbers, canonical rows, and the
 // skyline's per-attribute range (lo / hi) for the partitioning; the sort-key
 // range is cleared for the partition sort.
 template <int D>
 __global__ void __launch_bounds__(kCT)
 k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyflag,
-              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows, WsHeader *h, long long nb_raw) {
+              const uint32_t *blocksum, int64_t *sky_idx, uint32_t *sky_rows, WsHeader *h, long long nb) {
     __shared__ uint32_t blo[D], bhi[D];
     if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
     if (blockIdx.x == 0 && threadIdx.x == 0) { h->key_min = ~0ull; h->key_max = 0ull; }
     uint32_t lo[D], hi[D];
     #pragma unroll
     for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
+    // raw per-segment counts (from k_final): this block's offset is the sum of the
+    // counts before it, S the sum of all
     uint32_t run;
-    if (nb_raw) {
-        // raw per-segment counts (from k_final): this block's offset is the sum of the
-        // counts before it, S the sum of all
+    {
         uint32_t before = 0, all = 0;
-        for (long long j = threadIdx.x; j < nb_raw; j += kCT) {
+        for (long long j = threadIdx.x; j < nb; j += kCT) {
             const uint32_t c = blocksum[j];
             before += j < (long long)blockIdx.x ? c : 0u;
             all += c;
@@ -734,8 +817,6 @@ k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyfla
         block_scan(all, &ta);
         run = tb;
         if (blockIdx.x == 0 && threadIdx.x == 0) h->n_sky = ta;
-    } else {
-        run = blocksum[blockIdx.x];
     }
     const long long b0 = (long long)blockIdx.x * kCB;
     #pragma unroll 1
@@ -791,7 +872,8 @@ k_surv_cluster(Workspace ws) {
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     WsHeader *h = ws.hdr;
-    const long long M = h->n_surv;   // <= n <= kClCTAs * kClSmemCap
+    const long long M = h->n_surv;
+    if (M > kClusterSortMax) return;   // k_surv_sort_coop sorts them (every CTA returns here)
     if (tid == 0) { kr[0] = ~0ull; kr[1] = 0ull; }
     __syncthreads();
     // this CTA's positions [b0, b0 + cnt) of the (key, survivor) pairs, in shared memory
@@ -872,13 +954,12 @@ template <int D>
 cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Workspace &ws,
                       int64_t *d_sky_idx, cudaStream_t st, bool gres_reps) {
     const long long nb = (n + kCB - 1) / kCB;
-    const int gb = (int)std::min<long long>((n + 255) / 256, 152LL * 4);
     cudaError_t e = cudaSuccess;   // the selection histograms were zeroed with the header
     const int hb = (int)std::min<long long>((n + 1023) / 1024, 152LL * 2);
     k_keys<D><<<hb, 1024, 0, st>>>(d_data, n, dir, ws.keys[0], ws.hdr, ws.sel_hist, reps); note_launch();
     k_sel_l2<D><<<hb, kMaxReps, 0, st>>>(ws.keys[0], n, ws.hdr, ws.sel_hist + kSelBuckets, reps, ws.keys[1],
                                          ws.rep_idx, d_data, dir, ws.reps, ws.blocksum, nb,
-                                         gres_reps ? ws.greps : nullptr); note_launch();
+                                         gres_reps ? ws.greps : nullptr, ws.kill); note_launch();
     static int filter_blocks = 0;   // resident blocks of k_filter<D> on this GPU
     if (filter_blocks == 0) {
         int per_sm = 0, dev = 0, sms = 0;
@@ -889,29 +970,29 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     }
     const long long fchunks = (n + kFilterChunk - 1) / kFilterChunk;
     const int fb = (int)std::min<long long>(fchunks, (long long)filter_blocks);
-    k_filter<D><<<fb, kFilterThreads, 0, st>>>(d_data, dir, n, ws.reps, ws.hdr, ws.flags, ws.blocksum, nb); note_launch();
-    const bool small = n <= kClusterSortMax;
+    const int pb = (int)std::min<long long>((n + kPreThreads - 1) / kPreThreads, 152LL * 8);
+    k_prefilter<D><<<pb, kPreThreads, 0, st>>>(d_data, dir, n, ws.kill, ws.hdr, ws.flags, ws.vals[1]); note_launch();
+    k_filter<D><<<fb, kFilterThreads, 0, st>>>(d_data, dir, ws.vals[1], ws.reps, ws.hdr, ws.flags, ws.blocksum, nb);
+    note_launch();
+    // the survivors and the flags they leave cleared for k_final
     k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
-                                                     ws.surv_orig, ws.hdr, small ? 1 : 0); note_launch();
-    if (small) {
-        static bool configured = false;
-        e = launch_cluster(k_surv_cluster<D>, kClSmemBytes, &configured, st, ws);
+                                                     ws.surv_orig, ws.hdr, 1); note_launch();
+    // The survivor sort: in one cluster up to kClusterSortMax survivors, else with the
+    // grid-wide kernels. The survivor count is known on the device only, so above
+    // that many input rows both are queued and each returns at once for the other size.
+    static bool configured = false;
+    e = launch_cluster(k_surv_cluster<D>, kClSmemBytes, &configured, st, ws);
+    if (e != cudaSuccess) return e;
+    if (n > kClusterSortMax) {
+        static int coop = 0;
+        if (!coop && (e = coop_blocks(k_surv_sort_coop<D>, &coop)) != cudaSuccess) return e;
+        e = launch_coop(k_surv_sort_coop<D>, coop, st, ws);
         if (e != cudaSuccess) return e;
-    } else {
-        k_surv_keys<D><<<gb, 256, 0, st>>>(ws.surv_rows, ws.hdr, ws.keys[0], ws.vals[0], ws.flags, n); note_launch();
-        e = launch_radix_sort(ws, n, &ws.hdr->n_surv, surv_sort_passes(D), st);
-        if (e != cudaSuccess) return e;
-        const long long t2max = ((n + kTileRows - 1) / kTileRows + 31) / 32;
-        k_gather_tiles<D><<<(unsigned)t2max, 1024, 0, st>>>(ws.surv_rows, ws.surv_orig, ws.vals[0], ws.vals[1],
-                                                           ws.hdr, ws.cand, ws.perm, ws.tmin, ws.smin); note_launch();
     }
     k_final<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
-        ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags, small ? ws.blocksum : nullptr); note_launch();
-    if (!small) {
-        k_count_flags<<<(unsigned)nb, kCT, 0, st>>>(ws.flags, n, ws.blocksum, nb, ws.hdr); note_launch();
-    }
+        ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags, ws.blocksum); note_launch();
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
-                                                    ws.sky_rows, ws.hdr, small ? nb : 0); note_launch();
+                                                    ws.sky_rows, ws.hdr, nb); note_launch();
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ MIN, MAX = 0, 1
 PART_NONE, PART_GRID, PART_ANGULAR, PART_SLICED = 0, 1, 2, 3
 FLAG_COUNT_TESTS = 1
 FLAG_GRES_REPS = 2
+FLAG_COUNT_PARTS = 4
 
 _STATUS = {0: "GRES_OK", 1: "GRES_EINVAL", 2: "GRES_ENOMEM", 3: "GRES_EAGAIN",
            4: "GRES_ETIMEOUT", 5: "GRES_ECUDA", 6: "GRES_EINTERNAL"}
@@ -61,9 +62,20 @@ class Instance(ctypes.Structure):
 
 
 def plan(scheme: int = PART_GRID, m: int = 0, p: int = 0, slice_dim: int = 0, reps: int = 0,
-         slots: int = 0, count_tests: bool = False, gres_reps: bool = False) -> PlanCfg:
-    flags = (FLAG_COUNT_TESTS if count_tests else 0) | (FLAG_GRES_REPS if gres_reps else 0)
+         slots: int = 0, count_tests: bool = False, gres_reps: bool = False,
+         count_parts: bool = False) -> PlanCfg:
+    flags = ((FLAG_COUNT_TESTS if count_tests or count_parts else 0) | (FLAG_GRES_REPS if gres_reps else 0)
+             | (FLAG_COUNT_PARTS if count_parts else 0))
     return PlanCfg(scheme, m, p, slice_dim, reps, slots, flags, 0)
+
+
+def plan_partitions(cfg: PlanCfg | None, d: int) -> int:
+    """Partitions P of a plan for d attributes (the per-partition counts of count_parts
+    need a tests tensor of 2 + 4 P int64)."""
+    out = _i64(0)
+    _check(load().gres_plan_partitions(ctypes.byref(cfg) if cfg is not None else None, int(d),
+                                       ctypes.byref(out)))
+    return int(out.value)
 
 
 def library_path() -> str:
@@ -94,6 +106,8 @@ def load():
                                        _p, _p, _p, _p]
         lib.gres_udiv_magic.argtypes = [_u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
                                         ctypes.POINTER(_u32)]
+        lib.gres_barrier_probe.argtypes = [_i32, _p, _p, ctypes.POINTER(_u32)]
+        lib.gres_plan_partitions.argtypes = [ctypes.POINTER(PlanCfg), _i32, ctypes.POINTER(_i64)]
         lib.gres_test_peak_probe.argtypes = [_i32, _i32, _i32, _p, _p, ctypes.POINTER(ctypes.c_double)]
         lib.gres_launch_count.restype = ctypes.c_ulonglong
         lib.gres_launch_count.argtypes = []
@@ -133,7 +147,7 @@ def load():
                      "gres_timing_enable", "gres_timing_read", "gres_dataset_create",
                      "gres_dataset_destroy", "gres_dataset_info", "gres_dataset_sky_idx",
                      "gres_query_workspace_size", "gres_query", "gres_batch_workspace_size",
-                     "gres_batch", "gres_test_peak_probe"):
+                     "gres_batch", "gres_test_peak_probe", "gres_barrier_probe", "gres_plan_partitions"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -188,6 +202,15 @@ def test_peak_probe(d: int, iters: int, sink, blocks: int = 0, stream=None) -> f
     _check(load().gres_test_peak_probe(int(d), int(iters), int(blocks), _ptr(sink), _stream_ptr(stream),
                                        ctypes.byref(ops)))
     return float(ops.value)
+
+
+def barrier_probe(absent: int, stream=None) -> tuple[int, int]:
+    """Runs the bounded grid-wide wait check (gres_barrier_probe): (status code, status word)."""
+    torch = _torch()
+    words = torch.zeros(4, dtype=torch.int32, device="cuda")
+    st = _u32(0)
+    rc = load().gres_barrier_probe(int(absent), _ptr(words), _stream_ptr(stream), ctypes.byref(st))
+    return int(rc), int(st.value)
 
 
 # ---- torch-side helpers (device memory and streams) ---------------------------
