@@ -351,9 +351,10 @@ __device__ __forceinline__ void rep_sort_block(const uint32_t *data, int dir, co
         // The first filter pass's representatives: one per run of 32 in this spatial
         // order (kKillers = 32 runs at most), the one whose dominated region covers
         // the largest part of the data's box (score: the sum of log2(dhi_q - x_q + 1),
-        // the log of the box volume above x; ties to the first). Spread over the runs,
-        // they cover different parts of the data. A speed-only choice: correctness
-        // never depends on it. Sentinel rows stand in for missing runs.
+        // the log of the box volume above x; ties to the first), then ordered by
+        // that score, strongest first. Spread over the runs, they cover different
+        // parts of the data. A speed-only choice: correctness never depends on it.
+        // Sentinel rows stand in for missing runs. sk is free after the sort.
         static_assert(kKillers == kMaxReps / 32, "one first-pass representative per run");
         constexpr int DP = padded_dims(D);
         const int lane = tid & 31, w = tid >> 5;
@@ -373,11 +374,34 @@ __device__ __forceinline__ void rep_sort_block(const uint32_t *data, int dir, co
         uint32_t y[D];
         #pragma unroll
         for (int q = 0; q < D; q++) y[q] = __shfl_sync(0xffffffffu, x[q], src);
+        unsigned long long *kkey = sk;                              // per run: score | run
+        uint32_t *krow = reinterpret_cast<uint32_t *>(sk + 32);     // per run: its row
         if (lane == 0) {
-            if (key) store_row<D>(kill, w, y);
-            else {
+            kkey[w] = key ? ((key >> 32) << 32) | (unsigned long long)w : 0ull;
+            #pragma unroll
+            for (int q = 0; q < D; q++) krow[w * D + q] = y[q];
+        }
+        __syncthreads();
+        if (w == 0) {
+            // strongest first: a bitonic sort of the 32 run keys, descending
+            unsigned long long v2 = kkey[lane];
+            for (int size = 2; size <= 32; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, v2, stride);
+                    const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+                    const unsigned long long mn = other < v2 ? other : v2, mx = other < v2 ? v2 : other;
+                    v2 = (up == lower) ? mx : mn;
+                }
+            }
+            if (v2) {
+                const int rw = (int)(v2 & 31ull);
+                uint32_t z[D];
                 #pragma unroll
-                for (int q = 0; q < DP; q++) kill[w * DP + q] = kSentinel;
+                for (int q = 0; q < D; q++) z[q] = krow[rw * D + q];
+                store_row<D>(kill, lane, z);
+            } else {
+                #pragma unroll
+                for (int q = 0; q < DP; q++) kill[lane * DP + q] = kSentinel;
             }
         }
     }
@@ -457,48 +481,98 @@ k_sel_l2(const unsigned long long *keys, long long n, WsHeader *h, uint32_t *his
 // compares each; on anticorrelated data it drops few and adds a few percent
 // to the filter's cost.
 constexpr int kPreThreads = 256;
+constexpr int kPreRows = 4;                             // rows per thread and chunk
+constexpr int kPreChunk = kPreThreads * kPreRows;       // rows per block and chunk
+constexpr int kPreA = 4;                                // representatives tested on every row
+template <int D>
+__device__ __forceinline__ void kill_row(const uint4 *ks, int k, uint32_t (&sv)[D]) {
+    constexpr int DP = padded_dims(D);
+    const uint4 a = ks[k * (DP / 4)];
+    sv[0] = a.x;
+    if (D > 1) sv[1 < D ? 1 : 0] = a.y;
+    if (D > 2) sv[2 < D ? 2 : 0] = a.z;
+    if (D > 3) sv[3 < D ? 3 : 0] = a.w;
+    if (DP == 8) {
+        const uint4 b = ks[k * (DP / 4) + (DP == 8 ? 1 : 0)];
+        if (D > 4) sv[4 < D ? 4 : 0] = b.x;
+        if (D > 5) sv[5 < D ? 5 : 0] = b.y;
+        if (D > 6) sv[6 < D ? 6 : 0] = b.z;
+        if (D > 7) sv[7 < D ? 7 : 0] = b.w;
+    }
+}
+
+// Appends row i (when live) to the block's list lst (counter *cnt) with one
+// shared atomic per warp.
+__device__ __forceinline__ void block_append(bool live, uint32_t i, uint32_t *lst, unsigned *cnt) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, live);
+    unsigned pos = 0;
+    if (lane == 0 && m) pos = atomicAdd(cnt, (unsigned)__popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (live) lst[pos + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+// Blocks take chunks of kPreChunk rows: every row against the kPreA strongest
+// representatives, then the rows left against the others (compacted, one per
+// thread); the chunk's surviving rows go to the list with one global atomic.
 template <int D>
 __global__ void __launch_bounds__(kPreThreads)
 k_prefilter(const uint32_t *data, int dir, long long n, const uint32_t *kill, WsHeader *h, uint32_t *flags,
             uint32_t *alive) {
     constexpr int DP = padded_dims(D);
     __shared__ uint4 ks[kKillers * DP / 4];
+    __shared__ uint32_t lst[kPreChunk];   // rows left by the first kPreA representatives
+    __shared__ uint32_t buf[kPreChunk];   // the chunk's surviving rows
+    __shared__ unsigned cnt_a, cnt, base;
     for (int j = threadIdx.x; j < kKillers * DP / 4; j += blockDim.x) ks[j] = reinterpret_cast<const uint4 *>(kill)[j];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
-        const long long i = base + threadIdx.x;
-        const bool valid = i < n;
-        uint32_t x[D];
-        if (valid) load_canon<D>(data, i, dir, x);
-        else {
-            #pragma unroll
-            for (int q = 0; q < D; q++) x[q] = 0u;
-        }
-        bool live = valid;
-        for (int k = 0; k < kKillers; k++) {
-            if (!__any_sync(0xffffffffu, live)) break;
-            uint32_t sv[D];
-            const uint4 a = ks[k * (DP / 4)];
-            sv[0] = a.x;
-            if (D > 1) sv[1 < D ? 1 : 0] = a.y;
-            if (D > 2) sv[2 < D ? 2 : 0] = a.z;
-            if (D > 3) sv[3 < D ? 3 : 0] = a.w;
-            if (DP == 8) {
-                const uint4 b = ks[k * (DP / 4) + (DP == 8 ? 1 : 0)];
-                if (D > 4) sv[4 < D ? 4 : 0] = b.x;
-                if (D > 5) sv[5 < D ? 5 : 0] = b.y;
-                if (D > 6) sv[6 < D ? 6 : 0] = b.z;
-                if (D > 7) sv[7 < D ? 7 : 0] = b.w;
+    for (long long c0 = (long long)blockIdx.x * kPreChunk; c0 < n; c0 += (long long)gridDim.x * kPreChunk) {
+        if (threadIdx.x == 0) { cnt_a = 0; cnt = 0; }
+        __syncthreads();
+        #pragma unroll 1
+        for (int r = 0; r < kPreRows; r++) {
+            const long long i = c0 + (long long)r * kPreThreads + threadIdx.x;
+            const bool valid = i < n;
+            bool live = valid;
+            if (valid) {
+                uint32_t x[D];
+                load_canon<D>(data, i, dir, x);
+                #pragma unroll
+                for (int k = 0; k < kPreA; k++) {
+                    uint32_t sv[D];
+                    kill_row<D>(ks, k, sv);
+                    live = live && !dominates<D>(sv, x);
+                }
+                if (!live) flags[i] = 0u;
             }
-            live = live && !dominates<D>(sv, x);
+            block_append(live, (uint32_t)i, lst, &cnt_a);
         }
-        if (valid && !live) flags[i] = 0u;
-        const unsigned m = __ballot_sync(0xffffffffu, live);
-        unsigned pos = 0;
-        if (lane == 0 && m) pos = atomicAdd(&h->n_alive, (unsigned)__popc(m));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (live) alive[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+        __syncthreads();
+        const unsigned na = cnt_a;
+        for (unsigned j0 = 0; j0 < na; j0 += kPreThreads) {
+            const unsigned j = j0 + threadIdx.x;
+            const bool valid = j < na;
+            const uint32_t i = valid ? lst[j] : 0u;
+            uint32_t x[D];
+            if (valid) load_canon<D>(data, i, dir, x);
+            else {
+                #pragma unroll
+                for (int q = 0; q < D; q++) x[q] = 0u;
+            }
+            bool live = valid;
+            for (int k = kPreA; k < kKillers; k++) {
+                if (!__any_sync(0xffffffffu, live)) break;
+                uint32_t sv[D];
+                kill_row<D>(ks, k, sv);
+                live = live && !dominates<D>(sv, x);
+            }
+            if (valid && !live) flags[i] = 0u;
+            block_append(live, i, buf, &cnt);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base = cnt ? atomicAdd(&h->n_alive, cnt) : 0u;
+        __syncthreads();
+        for (unsigned j = threadIdx.x; j < cnt; j += kPreThreads) alive[base + j] = buf[j];
+        __syncthreads();
     }
 }
 
@@ -970,7 +1044,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     }
     const long long fchunks = (n + kFilterChunk - 1) / kFilterChunk;
     const int fb = (int)std::min<long long>(fchunks, (long long)filter_blocks);
-    const int pb = (int)std::min<long long>((n + kPreThreads - 1) / kPreThreads, 152LL * 8);
+    const int pb = (int)std::min<long long>((n + kPreChunk - 1) / kPreChunk, 152LL * 8);
     k_prefilter<D><<<pb, kPreThreads, 0, st>>>(d_data, dir, n, ws.kill, ws.hdr, ws.flags, ws.vals[1]); note_launch();
     k_filter<D><<<fb, kFilterThreads, 0, st>>>(d_data, dir, ws.vals[1], ws.reps, ws.hdr, ws.flags, ws.blocksum, nb);
     note_launch();
