@@ -403,7 +403,7 @@ gres_status gres_timing_read(double *ms, int64_t *launches, int32_t nstages);
  * (it can synchronize the device) -- and so cannot provide d_ws.
  * Same arguments and results as gres_compute, minus d_ws/ws_bytes/d_tests.
  * Scratch: one static device array of gres_static_scratch_bytes() bytes
- * (16 MiB: about 190,000 rows at d <= 4, 120,000 at d = 8, with up to 4,096
+ * (16 MiB: about 177,000 rows at d <= 4, 116,000 at d = 8, with up to 4,096
  * widths) inside the library, held on every GPU that loads the library until
  * the process exits. Sizes whose gres_workspace_size exceeds it give
  * GRES_EINVAL and nothing is launched. The call allocates nothing (no

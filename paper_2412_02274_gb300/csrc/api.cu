@@ -206,6 +206,8 @@ size_t workspace_layout(int64_t n, int d, int k, void *base, Workspace *ws) {
     w.cand = static_cast<uint32_t *>(take(4 * DP * rows_pad));
     w.tmin = static_cast<uint32_t *>(take(4 * DP * tiles));
     w.smin = static_cast<uint32_t *>(take(4 * DP * (tiles / 32 + 1)));
+    w.tsum = static_cast<unsigned long long *>(take(8 * (size_t)tiles));
+    w.ssum = static_cast<unsigned long long *>(take(8 * (size_t)(tiles / 32 + 1)));
     w.perm = static_cast<uint32_t *>(take(4 * nn));
     w.res = static_cast<int32_t *>(take(4 * nn));
     w.greps = static_cast<uint32_t *>(take(4 * DP * 32));

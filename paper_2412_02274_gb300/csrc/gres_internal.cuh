@@ -69,7 +69,7 @@ struct Workspace {
     uint32_t *vals[2];            // radix sort value ping-pong, n each
     uint32_t *hist;               // 256 * sort_blocks(n)
     uint32_t *dtot;               // 256 digit totals of the current pass
-    uint32_t *blocksum;           // compaction block sums
+    uint32_t *blocksum;           // skyline rows per kCB-row segment of the input (compaction offsets)
     uint32_t *flags;              // n
     uint32_t *surv_rows;          // n * DP canonical rows, sum order
     uint32_t *surv_orig;          // n original row numbers, sum order
@@ -80,6 +80,8 @@ struct Workspace {
     uint32_t *cand;               // (n + tile) * DP canonical rows, partition order
     uint32_t *tmin;               // tiles * DP per-tile minima
     uint32_t *smin;               // super-tiles (1024 rows) * DP minima
+    unsigned long long *tsum;     // per survivor tile: its smallest row sum (sentinel tiles: ~0)
+    unsigned long long *ssum;     // per survivor super-tile: its smallest row sum
     uint32_t *perm;               // n: partition position -> skyline position
     int32_t *res;                 // n: per partition position, a bound on the result (GRES_FLAG_GRES_REPS)
     uint32_t *greps;              // 32 * DP: the gres-stage representatives (GRES_FLAG_GRES_REPS)

@@ -88,6 +88,23 @@ __device__ __forceinline__ bool dominates(const uint32_t (&s)[D], const uint32_t
     return le && lt;
 }
 
+// Smallest row sum over the warp's rows (~0 for lanes without a row): a tile
+// can hold a dominator of x only if some row sums to less than x (Def. 1 on
+// canonical values implies a strictly smaller sum).
+template <int D, int DP>
+__device__ __forceinline__ unsigned long long warp_min_sum(const uint32_t (&x)[DP], bool valid) {
+    unsigned long long v = 0;
+    #pragma unroll
+    for (int q = 0; q < D; q++) v += x[q];
+    if (!valid) v = ~0ull;
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
+        v = y < v ? y : v;
+    }
+    return v;
+}
+
 // Morton code of x - lo over `bits` bits per attribute (D * bits <= 32):
 // coordinate i is quantized to floor((x_i - lo_i) 2^bits / (hi_i - lo_i + 1)).
 template <int D>
@@ -279,8 +296,8 @@ __device__ __forceinline__ unsigned long long block_bitonic(unsigned long long v
 // and writes their canonical rows to `rows` in that order. Spatially tight
 // runs of 32 representatives let the filter skip whole runs. Representatives
 // dominated by another representative stay: by transitivity the filter drops
-// exactly the same rows with or without them. Also clears the filter's
-// per-segment survivor counts (nb of them). greps (may be NULL): also the 32
+// exactly the same rows with or without them. Also clears the per-segment
+// skyline counts that k_final fills (nb of them). greps (may be NULL): also the 32
 // candidates of smallest f, canonical rows padded with sentinel rows, for the
 // gres stage's representatives. Run by one block of kMaxReps threads (all of
 // them); nc = the number of candidates in rep_idx; sk, xs, lo, hi: shared
@@ -525,6 +542,10 @@ k_prefilter(const uint32_t *data, int dir, long long n, const uint32_t *kill, Ws
     __shared__ uint32_t buf[kPreChunk];   // the chunk's surviving rows
     __shared__ unsigned cnt_a, cnt, base;
     for (int j = threadIdx.x; j < kKillers * DP / 4; j += blockDim.x) ks[j] = reinterpret_cast<const uint4 *>(kill)[j];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // the sort-key range, cleared for the survivor sort
+        h->key_min = ~0ull;
+        h->key_max = 0ull;
+    }
     for (long long c0 = (long long)blockIdx.x * kPreChunk; c0 < n; c0 += (long long)gridDim.x * kPreChunk) {
         if (threadIdx.x == 0) { cnt_a = 0; cnt = 0; }
         __syncthreads();
@@ -576,9 +597,13 @@ k_prefilter(const uint32_t *data, int dir, long long n, const uint32_t *kill, Ws
     }
 }
 
-// Survivor flags (not dominated by any representative) of the rows the first
-// pass left (alive, h->n_alive of them, in any order), plus per-segment
-// survivor counts (kCB-row segments of the input) for the compaction. The
+// The rows the first pass left (alive, h->n_alive of them, in any order)
+// against all the representatives. Survivors (rows no representative
+// dominates) are listed, in no particular order, as canonical rows
+// (surv_rows), original row numbers (surv_orig) and their count (n_surv),
+// with their per-attribute range (slo / shi) for the spatial order; the
+// flags of all the rows looked at are set to 0 (k_final sets the skyline
+// rows' flags). The
 // representatives sit in shared memory (attribute-major) in runs of 32 with
 // each run's per-attribute minimum; a run can hold a dominator of x only if
 // its minimum is <= x in every attribute. Each lane keeps the minimum of run
@@ -594,9 +619,16 @@ constexpr int kFilterChunk = (kFilterThreads / 32) * kFilterRowsPerWarp;
 template <int D>
 __global__ void __launch_bounds__(kFilterThreads)
 k_filter(const uint32_t *data, int dir, const uint32_t *alive, const uint32_t *reps, WsHeader *h,
-         uint32_t *flags, uint32_t *blocksum, long long nb) {
+         uint32_t *flags, uint32_t *surv_rows, uint32_t *surv_orig) {
+    constexpr int DP = padded_dims(D);
     __shared__ uint32_t rs[D * kMaxReps];
     __shared__ uint32_t rmin[D * (kMaxReps / 32)];
+    __shared__ uint32_t srow[kFilterChunk];        // the chunk's survivors, listed at once
+    __shared__ uint32_t sx[kFilterChunk * DP];
+    __shared__ unsigned scnt;
+    __shared__ unsigned long long sbase;
+    __shared__ uint32_t blo[D], bhi[D];
+    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
     const int nr = (int)h->n_reps;
     const int nruns = (nr + 31) / 32;
     const long long na = h->n_alive;
@@ -622,86 +654,70 @@ k_filter(const uint32_t *data, int dir, const uint32_t *alive, const uint32_t *r
     #pragma unroll
     for (int q = 0; q < D; q++) mn[q] = lane < nruns ? rmin[q * (kMaxReps / 32) + lane] : 0xFFFFFFFFu;
     const bool run_ok = lane < nruns;
-    for (long long c0 = (long long)blockIdx.x * kFilterChunk; c0 < na; c0 += (long long)gridDim.x * kFilterChunk) {
-        const long long g0 = c0 + (long long)warp * kFilterRowsPerWarp;
-        if (g0 >= na) continue;
-        const int lim = (int)min((long long)kFilterRowsPerWarp, na - g0);
-        uint32_t x[D];
-        const uint32_t row = lane < lim ? __ldcg(alive + g0 + lane) : 0u;
-        if (lane < lim) load_canon<D>(data, row, dir, x);
-        else {
-            #pragma unroll
-            for (int q = 0; q < D; q++) x[q] = 0u;
-        }
-        unsigned alive_mask = 0;
-        for (int l = 0; l < lim; l++) {
-            uint32_t xs[D];
-            #pragma unroll
-            for (int q = 0; q < D; q++) xs[q] = __shfl_sync(0xffffffffu, x[q], l);
-            bool maybe = run_ok;
-            #pragma unroll
-            for (int q = 0; q < D; q++) maybe &= mn[q] <= xs[q];
-            unsigned runs = __ballot_sync(0xffffffffu, maybe);
-            bool dom = false;
-            while (runs && !dom) {
-                const int rr = __ffs(runs) - 1;
-                runs &= runs - 1;
-                const int j = rr * 32 + lane;
-                uint32_t sv[D];
-                #pragma unroll
-                for (int q = 0; q < D; q++) sv[q] = rs[q * kMaxReps + j];
-                dom = __any_sync(0xffffffffu, j < nr && dominates<D>(sv, xs));
-            }
-            if (!dom) alive_mask |= 1u << l;
-        }
-        if (lane < lim) {
-            const uint32_t f = (alive_mask >> lane) & 1u;
-            flags[row] = f;
-            if (f) atomicAdd(&blocksum[row / kCB], 1u);
-        }
-    }
-    if (last_block_done(&h->done[2])) {
-        // survivors' offsets; the sort-key range is cleared for the survivor sort
-        const uint32_t total = block_scan_inplace(blocksum, nb);
-        if (threadIdx.x == 0) {
-            h->n_surv = total;
-            h->key_min = ~0ull;
-            h->key_max = 0ull;
-        }
-    }
-}
-
-// Survivors in input order: canonical rows, original row numbers, and their
-// per-attribute range (slo / shi) for the spatial order. With `clear`, the
-// flags read and the block's segment offset are reset to 0 for k_final.
-template <int D>
-__global__ void __launch_bounds__(kCT)
-k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, uint32_t *blocksum,
-               uint32_t *surv_rows, uint32_t *surv_orig, WsHeader *h, int clear) {
-    __shared__ uint32_t blo[D], bhi[D];
-    if (threadIdx.x < D) { blo[threadIdx.x] = 0xFFFFFFFFu; bhi[threadIdx.x] = 0u; }
-    uint32_t run = blocksum[blockIdx.x];
-    const long long b0 = (long long)blockIdx.x * kCB;
     uint32_t lo[D], hi[D];
     #pragma unroll
     for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
-    #pragma unroll 1
-    for (int r = 0; r < kPer; r++) {
-        const long long p = b0 + r * kCT + threadIdx.x;
-        const uint32_t f = p < n ? flags[p] : 0u;
-        if (clear && f) flags[p] = 0u;   // cleared for k_final
-        uint32_t tot;
-        const uint32_t ex = block_scan(f, &tot);
-        if (f) {
+    for (long long c0 = (long long)blockIdx.x * kFilterChunk; c0 < na; c0 += (long long)gridDim.x * kFilterChunk) {
+        if (threadIdx.x == 0) scnt = 0;
+        __syncthreads();
+        const long long g0 = c0 + (long long)warp * kFilterRowsPerWarp;
+        if (g0 < na) {
+            const int lim = (int)min((long long)kFilterRowsPerWarp, na - g0);
             uint32_t x[D];
-            load_canon<D>(data, p, dir, x);
-            store_row<D>(surv_rows, run + ex, x);
-            surv_orig[run + ex] = (uint32_t)p;
-            #pragma unroll
-            for (int q = 0; q < D; q++) { lo[q] = min(lo[q], x[q]); hi[q] = max(hi[q], x[q]); }
+            const uint32_t row = lane < lim ? __ldcg(alive + g0 + lane) : 0u;
+            if (lane < lim) load_canon<D>(data, row, dir, x);
+            else {
+                #pragma unroll
+                for (int q = 0; q < D; q++) x[q] = 0u;
+            }
+            unsigned alive_mask = 0;
+            for (int l = 0; l < lim; l++) {
+                uint32_t xs[D];
+                #pragma unroll
+                for (int q = 0; q < D; q++) xs[q] = __shfl_sync(0xffffffffu, x[q], l);
+                bool maybe = run_ok;
+                #pragma unroll
+                for (int q = 0; q < D; q++) maybe &= mn[q] <= xs[q];
+                unsigned runs = __ballot_sync(0xffffffffu, maybe);
+                bool dom = false;
+                while (runs && !dom) {
+                    const int rr = __ffs(runs) - 1;
+                    runs &= runs - 1;
+                    const int j = rr * 32 + lane;
+                    uint32_t sv[D];
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) sv[q] = rs[q * kMaxReps + j];
+                    dom = __any_sync(0xffffffffu, j < nr && dominates<D>(sv, xs));
+                }
+                if (!dom) alive_mask |= 1u << l;
+            }
+            if (lane < lim) flags[row] = 0u;
+            const bool keep = lane < lim && ((alive_mask >> lane) & 1u);
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            unsigned pos = 0;
+            if (lane == 0 && m) pos = atomicAdd(&scnt, (unsigned)__popc(m));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (keep) {
+                const unsigned slot = pos + __popc(m & ((1u << lane) - 1u));
+                srow[slot] = row;
+                #pragma unroll
+                for (int q = 0; q < DP; q++) sx[slot * DP + q] = q < D ? x[q < D ? q : 0] : 0u;
+                #pragma unroll
+                for (int q = 0; q < D; q++) { lo[q] = min(lo[q], x[q]); hi[q] = max(hi[q], x[q]); }
+            }
         }
-        run += tot;
+        __syncthreads();
+        if (threadIdx.x == 0 && scnt)
+            sbase = atomicAdd(reinterpret_cast<unsigned long long *>(&h->n_surv), (unsigned long long)scnt);
+        __syncthreads();
+        for (unsigned j = threadIdx.x; j < scnt; j += kFilterThreads) {
+            surv_orig[sbase + j] = srow[j];
+            #pragma unroll
+            for (int q = 0; q < DP; q++) surv_rows[(sbase + j) * DP + q] = sx[j * DP + q];
+        }
+        __syncthreads();
     }
+    // the survivors' range
     #pragma unroll
     for (int q = 0; q < D; q++) {
         #pragma unroll
@@ -709,14 +725,13 @@ k_compact_surv(const uint32_t *data, int dir, long long n, uint32_t *flags, uint
             lo[q] = min(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
             hi[q] = max(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
         }
-        if ((threadIdx.x & 31) == 0) { atomicMin(&blo[q], lo[q]); atomicMax(&bhi[q], hi[q]); }
+        if (lane == 0 && lo[q] <= hi[q]) { atomicMin(&blo[q], lo[q]); atomicMax(&bhi[q], hi[q]); }
     }
     __syncthreads();
-    if (threadIdx.x < D) {
+    if (threadIdx.x < D && blo[threadIdx.x] <= bhi[threadIdx.x]) {
         atomicMin(&h->slo[threadIdx.x], blo[threadIdx.x]);
         atomicMax(&h->shi[threadIdx.x], bhi[threadIdx.x]);
     }
-    if (clear && threadIdx.x == 0) blocksum[blockIdx.x] = 0u;   // k_final counts skyline rows here
 }
 
 // Bits per attribute of the survivors' Morton code when more than
@@ -788,6 +803,8 @@ k_surv_sort_coop(Workspace ws) {
             for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
             if (lane == 0) ws.tmin[tile * DP + q] = m;
         }
+        const unsigned long long ms = warp_min_sum<D>(x, r < M);
+        if (lane == 0) ws.tsum[tile] = ms;
     }
     if (!grid_barrier(h->bar, &h->status, &s.ok)) return;
     // super-tile minima: one thread per super-tile and attribute word
@@ -799,12 +816,18 @@ k_surv_sort_coop(Workspace ws) {
         for (long long t = sup * 32; t < min(T, sup * 32 + 32); t++) m = min(m, ws.tmin[t * DP + q]);
         ws.smin[sup * DP + q] = m;
     }
+    for (long long sup = gt; sup < T2; sup += stride) {
+        unsigned long long m = ~0ull;
+        for (long long t = sup * 32; t < min(T, sup * 32 + 32); t++) m = min(m, ws.tsum[t]);
+        ws.ssum[sup] = m;
+    }
 }
 
 // Final filter over the survivors in spatial order: survivor x is a skyline
 // tuple iff no survivor dominates it (Def. 1). A tile (32 rows) or super-tile
 // (1024 rows) can hold a dominator only if its minimum is <= x in every
-// attribute -- the grid-dominance pruning of Sec. 3.1 on tiles. One warp per
+// attribute -- the grid-dominance pruning of Sec. 3.1 on tiles -- and if
+// its smallest row sum is below x's sum (a dominator's sum is smaller). One warp per
 // survivor: lanes test 32 super-tile minima, then the 32 tile minima of each
 // possible super-tile, then the 32 rows of each possible tile, stopping at the
 // first dominator. Sets skyflag[original row] and, with segcount, counts the
@@ -812,7 +835,8 @@ k_surv_sort_coop(Workspace ws) {
 template <int D>
 __global__ void __launch_bounds__(kTriThreads)
 k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const uint32_t *smin,
-        const WsHeader *h, uint32_t *skyflag, uint32_t *segcount) {
+        const unsigned long long *tsum, const unsigned long long *ssum, const WsHeader *h, uint32_t *skyflag,
+        uint32_t *segcount) {
     const long long M = h->n_surv;
     const long long T = (M + kTileRows - 1) / kTileRows;
     const long long T2 = (T + 31) / 32;
@@ -822,13 +846,16 @@ k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const 
     for (long long q = wid; q < M; q += nw) {
         uint32_t x[D];
         load_row<D>(rows, q, x);
+        unsigned long long xsum = 0;
+        #pragma unroll
+        for (int i = 0; i < D; i++) xsum += x[i];
         bool dom = false;
         for (long long s0 = 0; s0 < T2 && !dom; s0 += 32) {
             bool maybe = false;
             if (s0 + lane < T2) {
                 uint32_t m[D];
                 load_row<D>(smin, s0 + lane, m);
-                maybe = true;
+                maybe = __ldg(ssum + s0 + lane) < xsum;
                 #pragma unroll
                 for (int i = 0; i < D; i++) maybe &= m[i] <= x[i];
             }
@@ -841,7 +868,7 @@ k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const 
                 if (tile < T) {
                     uint32_t m[D];
                     load_row<D>(tmin, tile, m);
-                    tmaybe = true;
+                    tmaybe = __ldg(tsum + tile) < xsum;
                     #pragma unroll
                     for (int i = 0; i < D; i++) tmaybe &= m[i] <= x[i];
                 }
@@ -858,7 +885,7 @@ k_final(const uint32_t *rows, const uint32_t *orig, const uint32_t *tmin, const 
         if (!dom && lane == 0) {
             const uint32_t o = orig[q];
             skyflag[o] = 1u;
-            if (segcount) atomicAdd(&segcount[o / kCB], 1u);
+            atomicAdd(&segcount[o / kCB], 1u);
         }
     }
 }
@@ -876,6 +903,8 @@ k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyfla
     uint32_t lo[D], hi[D];
     #pragma unroll
     for (int q = 0; q < D; q++) { lo[q] = 0xFFFFFFFFu; hi[q] = 0u; }
+    // segments without skyline rows have nothing to do (block 0 still writes S)
+    if (blockIdx.x != 0 && blocksum[blockIdx.x] == 0u) return;
     // raw per-segment counts (from k_final): this block's offset is the sum of the
     // counts before it, S the sum of all
     uint32_t run;
@@ -934,7 +963,7 @@ k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyfla
 // The survivors' 16-bit Morton keys over their range, the stable sort by
 // key, and the survivor tiles in that order (rows, original row numbers, tile
 // and super-tile minima) -- the work of k_surv_keys, the radix sort and
-// k_gather_tiles, for the M survivors k_compact_surv left.
+// k_gather_tiles, for the M survivors k_filter listed.
 template <int D>
 __global__ void __launch_bounds__(kClThreads)
 k_surv_cluster(Workspace ws) {
@@ -942,6 +971,7 @@ k_surv_cluster(Workspace ws) {
     extern __shared__ uint32_t sm[];
     __shared__ unsigned long long kr[2];
     __shared__ uint32_t wm[32][DP];
+    __shared__ unsigned long long wsm[32];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -1008,6 +1038,11 @@ k_surv_cluster(Workspace ws) {
                 if (tile < T) ws.tmin[tile * DP + q] = m;
             }
         }
+        const unsigned long long ms = warp_min_sum<D>(x, row < M);
+        if (lane == 0) {
+            wsm[w] = ms;
+            if (tile < T) ws.tsum[tile] = ms;
+        }
         __syncthreads();
         if (w == 0) {
             #pragma unroll
@@ -1017,6 +1052,13 @@ k_surv_cluster(Workspace ws) {
                 for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
                 if (lane == 0) ws.smin[sup * DP + q] = m;
             }
+            unsigned long long m = wsm[lane];
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+                m = y < m ? y : m;
+            }
+            if (lane == 0) ws.ssum[sup] = m;
         }
         __syncthreads();
     }
@@ -1046,13 +1088,11 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
     const int fb = (int)std::min<long long>(fchunks, (long long)filter_blocks);
     const int pb = (int)std::min<long long>((n + kPreChunk - 1) / kPreChunk, 152LL * 8);
     k_prefilter<D><<<pb, kPreThreads, 0, st>>>(d_data, dir, n, ws.kill, ws.hdr, ws.flags, ws.vals[1]); note_launch();
-    k_filter<D><<<fb, kFilterThreads, 0, st>>>(d_data, dir, ws.vals[1], ws.reps, ws.hdr, ws.flags, ws.blocksum, nb);
+    k_filter<D><<<fb, kFilterThreads, 0, st>>>(d_data, dir, ws.vals[1], ws.reps, ws.hdr, ws.flags, ws.surv_rows,
+                                               ws.surv_orig);
     note_launch();
-    // the survivors and the flags they leave cleared for k_final
-    k_compact_surv<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, ws.surv_rows,
-                                                     ws.surv_orig, ws.hdr, 1); note_launch();
     // The survivor sort: in one cluster up to kClusterSortMax survivors, else with the
-    // grid-wide kernels. The survivor count is known on the device only, so above
+    // cooperative kernel. The survivor count is known on the device only, so above
     // that many input rows both are queued and each returns at once for the other size.
     static bool configured = false;
     e = launch_cluster(k_surv_cluster<D>, kClSmemBytes, &configured, st, ws);
@@ -1064,7 +1104,7 @@ cudaError_t skyline_d(const uint32_t *d_data, int64_t n, int dir, int reps, Work
         if (e != cudaSuccess) return e;
     }
     k_final<D><<<(unsigned)std::min<int64_t>((n + 7) / 8, 152LL * 16), kTriThreads, 0, st>>>(
-        ws.cand, ws.perm, ws.tmin, ws.smin, ws.hdr, ws.flags, ws.blocksum); note_launch();
+        ws.cand, ws.perm, ws.tmin, ws.smin, ws.tsum, ws.ssum, ws.hdr, ws.flags, ws.blocksum); note_launch();
     k_compact_sky<D><<<(unsigned)nb, kCT, 0, st>>>(d_data, dir, n, ws.flags, ws.blocksum, d_sky_idx,
                                                     ws.sky_rows, ws.hdr, nb); note_launch();
     return cudaGetLastError();
