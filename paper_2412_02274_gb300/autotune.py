@@ -96,7 +96,7 @@ class Autotuner:
     """Fastest candidate plan per size class, chosen by timing sample problems."""
 
     def __init__(self, candidates: list[Candidate] | None = None, timer=None, objective: str = "alone",
-                 concurrency: int = 16):
+                 concurrency: int = 16, default: str = "grid-auto-s8", margin: float = 0.05):
         if objective not in ("alone", "batch"):
             raise ValueError("objective must be 'alone' or 'batch'")
         self.candidates = list(candidates or default_candidates())
@@ -104,6 +104,10 @@ class Autotuner:
         self.timer = timer
         self.objective = objective
         self.concurrency = concurrency
+        # a candidate replaces the library's default plan only if it scores at least
+        # `margin` lower: single timings of the sample problems move by a few percent
+        self.default = default if default in self._by_name else None
+        self.margin = margin
         self.table: dict[tuple[int, int], str] = {}
         self.timings: dict[tuple[int, int], dict[str, float]] = {}
 
@@ -131,7 +135,10 @@ class Autotuner:
                     total[c.name] += score(timer(x, steps, direction, c.cfg(), ws), self.objective,
                                            self.concurrency)
             self.timings[cls] = total
-            self.table[cls] = min(self.candidates, key=lambda c: (total[c.name], c.name)).name
+            best = min(self.candidates, key=lambda c: (total[c.name], c.name)).name
+            if self.default and total[best] > (1.0 - self.margin) * total[self.default]:
+                best = self.default
+            self.table[cls] = best
         return dict(self.table)
 
     def plan_for(self, n: int, d: int) -> G.PlanCfg:

@@ -635,7 +635,7 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 // made on the fly for each slot test instead of being kept in registers.
 template <int D, int SLOTS, bool GM = false>
 __host__ __device__ constexpr int dom_threads() {
-    return GM ? 768 : 1024;
+    return GM ? (D <= 4 ? 768 : 640) : 1024;
 }
 
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
@@ -734,6 +734,13 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
         }
         __syncwarp();
         int best = wcount;
+        // The target's cell at the widths of one slot (canonical bounds per attribute).
+        // With the grid parameter g they cost two divisions per attribute, so the g
+        // form keeps the last slot's bounds (its step lists are short: usually one
+        // slot); with widths they are made for every test, which keeps the kernel at 64
+        // registers and 32 warps per SM.
+        uint32_t chi[D], clo[D];
+        int cj = -1;
         if (qy.ub) {
             // a known exit step (GRES_FLAG_GRES_REPS): only earlier steps are searched
             const int b = qy.ub[i];
@@ -847,17 +854,23 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                             // lanes past K never match
                             const int k = w0 + 32 * j + lane;
                             const bool live = k < K;
-                            const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
-                                                  : make_uint4(1u, 0u, 0u, 1u);
+                            if (GM ? cj != j : true) {
+                                const uint4 mg = live ? __ldg(reinterpret_cast<const uint4 *>(qy.magic) + k)
+                                                      : make_uint4(1u, 0u, 0u, 1u);
+                                #pragma unroll
+                                for (int q = 0; q < D; q++) {
+                                    uint32_t lv, uv;
+                                    raw_cell(qy.dir ? ~t[q] : t[q], mg, GM ? qy.gbits : 0, lv, uv);
+                                    chi[q] = live ? (qy.dir ? ~lv : uv) : 0u;
+                                    clo[q] = live ? (qy.dir ? ~uv : lv) : 0u;
+                                }
+                                cj = j;
+                            }
                             bool le = true, lt = false;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                uint32_t lv, uv;
-                                raw_cell(qy.dir ? ~t[q] : t[q], mg, GM ? qy.gbits : 0, lv, uv);
-                                const uint32_t hi = live ? (qy.dir ? ~lv : uv) : 0u;
-                                const uint32_t lo = live ? (qy.dir ? ~uv : lv) : 0u;
-                                le &= cv[q] <= hi;
-                                lt |= cv[q] < lo;
+                                le &= cv[q] <= chi[q];
+                                lt |= cv[q] < clo[q];
                             }
                             n_tests += 32;
                             if (pc.pcnt && lane == 0 && __ldg(pc.pid + i) < pc.nparts) {

@@ -73,3 +73,19 @@ def test_batch_objective_weights_the_shared_dominance_launch():
     alone = Autotuner(cands, timer=timer).tune([_Rows(5000, 4)], np.array([1, 2], np.uint32))
     batch = Autotuner(cands, timer=timer, objective="batch").tune([_Rows(5000, 4)], np.array([1, 2], np.uint32))
     assert alone[(4, 13)] == "none" and batch[(4, 13)] == "grid"
+
+
+def test_default_plan_kept_unless_beaten_by_the_margin():
+    """A candidate replaces the default plan (Grid, automatic m, 8 slots) only when it scores
+    at least 5% lower; a 2% gain, within the timing noise of single samples, keeps the default."""
+    def timer(gain):
+        def run(x, steps, direction, cfg, ws):
+            default = cfg.scheme == G.PART_GRID and cfg.m == 0 and cfg.slots == 8 and not cfg.flags
+            return 1.0 if default else (1.0 - gain if cfg.scheme == G.PART_NONE and cfg.slots == 8
+                                        and not cfg.flags else 2.0)
+        return run
+    probs = [_Rows(5000, 4)]
+    steps = np.arange(1, 9, dtype=np.uint32)
+    assert Autotuner(timer=timer(0.02)).tune(probs, steps)[size_class(5000, 4)] == "grid-auto-s8"
+    assert Autotuner(timer=timer(0.10)).tune(probs, steps)[size_class(5000, 4)] == "none-s8"
+    assert Autotuner(timer=timer(0.02), margin=0.0).tune(probs, steps)[size_class(5000, 4)] == "none-s8"
