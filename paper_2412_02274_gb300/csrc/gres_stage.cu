@@ -710,10 +710,28 @@ k_rep_bound(const uint32_t *cand, const uint32_t *greps, const long long *n_sky,
     if (tests && lane == 0 && n_tests) atomicAdd(tests, n_tests);
 }
 
+// Canonical row r of a candidate set, DP words apart: staged in shared memory
+// (RES) or read through L1.
+template <int D, bool RES>
+__device__ __forceinline__ void ld_cand(const uint32_t *base, long long r, uint32_t (&x)[D]) {
+    if (RES) ld_row<D>(base, r, x); else ldg_row<D>(base, r, x);
+}
+
+// Per attribute, the largest canonical value s with s - t < wl (wl >= 1):
+// min(t + wl - 1, 2^32 - 1). A candidate row's excess max_i (s_i - t_i)^+ is
+// below wl exactly when every s_i is at most this bound.
+template <int D>
+__device__ __forceinline__ void excess_bounds(const uint32_t (&t)[D], uint32_t wl, uint32_t (&thr)[D]) {
+    #pragma unroll
+    for (int q = 0; q < D; q++) thr[q] = min(t[q], 0xFFFFFFFFu - (wl - 1u)) + (wl - 1u);
+}
+
 // Grid resistance of the target at partition position i of query q (one
 // warp; every lane returns it): the first step at which some candidate's
-// projection dominates the target's projection, else K.
-template <int D, int SLOTS, bool RES, bool GM>
+// projection dominates the target's projection, else K. CNT: count the
+// lane-tests and pruning checks (GRES_FLAG_COUNT_TESTS / _PARTS); the search
+// is the same either way.
+template <int D, int SLOTS, bool RES, bool GM, bool CNT>
 __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
                                            const uint32_t *smin, long long T, unsigned i, uint32_t *wsteps,
                                            unsigned long long &n_tests, unsigned long long &n_checks,
@@ -722,7 +740,7 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
     const int lane = threadIdx.x & 31;
     const int K = qy.K;
     uint32_t t[D];
-    if (RES) ld_row<D>(cand, i, t); else ldg_row<D>(cand, i, t);
+    ld_cand<D, RES>(cand, i, t);
     int result = K;
     for (int w0 = 0; w0 < K; w0 += WS) {
         const int wcount = min(WS, K - w0);
@@ -749,15 +767,21 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
         // keys hold excesses >> qshift; only excesses below the window's widest width matter
         const uint32_t wmax = wsteps[wcount - 1];
         const int qshift = wmax >> 24 ? 32 - __clz(wmax) - 24 : 0;
-        // wl: the width of step best - 1 (excesses at or above it cannot matter), wlq: its key
-        uint32_t wl = best > 0 ? wsteps[best - 1] : 0u, wlq = min(wl >> qshift, 0x7FFFFFFu);
+        // wl: the width of step best - 1 (excesses at or above it cannot matter);
+        // wlq: the largest key whose excess can be below wl ((wl - 1) >> qshift; with
+        // qshift = 0 every key up to wlq is below wl, above 0 the keys equal to wlq
+        // are checked exactly); thr: the excess bounds of wl
+        uint32_t wl = best > 0 ? wsteps[best - 1] : 1u;
+        uint32_t wlq = min((wl - 1u) >> qshift, 0x7FFFFFFu);
+        uint32_t thr[D];
+        excess_bounds<D>(t, wl, thr);
         // lane j < SLOTS - 1 holds the widest width of slot j (for the first slot that can matter)
         const uint32_t slot_top = (lane < SLOTS - 1 && 32 * lane + 31 < wcount) ? wsteps[32 * lane + 31] : 0xFFFFFFFFu;
         // Best-first over two levels -- 1024-row super-tiles, then 32-row tiles --
         // each visited in ascending order of its lower bound on the excess
-        // max_i (s_i - t_i)^+ (keys hold it >> qshift, 27 bits; exact tests below),
-        // then the rows of a tile whose excess is below delta[best - 1].
-        // Anything whose bound reaches delta[best - 1] is skipped.
+        // max_i (s_i - t_i)^+ (keys hold it >> qshift, 27 bits), then the rows of a
+        // tile whose excess is below delta[best - 1]. Anything whose bound reaches
+        // delta[best - 1] is skipped.
         const long long T2 = (T + 31) / 32;
         for (long long s0 = 0; s0 < T2 && best > 0; s0 += 32) {
             uint32_t skey = kNoTile, sex = 0xFFFFFFFFu;
@@ -776,14 +800,13 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                     skey = (min(emax >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane;
                 }
             }
-            n_checks += 32;
+            if (CNT) n_checks += 32;
             for (;;) {
                 const uint32_t mk = __reduce_min_sync(kFull, skey);
-                if (mk == kNoTile) break;
-                if ((mk >> 5) > wlq) break;   // every super-tile left is too far
+                if (mk == kNoTile || (mk >> 5) > wlq) break;   // every super-tile left is too far
                 const int sl = (int)(mk & 31u);
                 if (lane == sl) skey = kNoTile;
-                if (__shfl_sync(kFull, sex, sl) >= wl) continue;
+                if (qshift && (mk >> 5) == wlq && __shfl_sync(kFull, sex, sl) >= wl) continue;
                 const long long sup = s0 + sl;
                 // tile level inside the super-tile: lane = tile
                 uint32_t tkey = kNoTile, tex = 0xFFFFFFFFu;
@@ -803,49 +826,52 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                         tkey = (min(emax >> qshift, 0x7FFFFFFu) << 5) | (uint32_t)lane;
                     }
                 }
-                n_checks += 32;
+                if (CNT) n_checks += 32;
                 for (;;) {
                     const uint32_t tk = __reduce_min_sync(kFull, tkey);
-                    if (tk == kNoTile) break;
-                    if ((tk >> 5) > wlq) break;   // every tile left is too far
+                    if (tk == kNoTile || (tk >> 5) > wlq) break;   // every tile left is too far
                     const int tl = (int)(tk & 31u);
                     if (lane == tl) tkey = kNoTile;
-                    if (__shfl_sync(kFull, tex, tl) >= wl) continue;
+                    if (qshift && (tk >> 5) == wlq && __shfl_sync(kFull, tex, tl) >= wl) continue;
                     const long long r0 = (sup * 32 + tl) * kTileRows;
                     // row level: lane r looks at row r of the tile; a row can dominate t
-                    // only at widths wider than its excess e_r, and it matters only if
-                    // such a width comes before best
-                    uint32_t e_r = 0;
-                    bool can_r = false;
+                    // only if some attribute is below t's and its excess is below wl (every
+                    // attribute within the excess bounds): only a width wider than the
+                    // excess, and before best, can make it dominate
+                    bool le = true, lt = false;
                     {
                         uint32_t s[D];
-                        if (RES) ld_row<D>(cand, r0 + lane, s); else ldg_row<D>(cand, r0 + lane, s);
+                        ld_cand<D, RES>(cand, r0 + lane, s);
                         #pragma unroll
                         for (int q = 0; q < D; q++) {
-                            e_r = max(e_r, s[q] > t[q] ? s[q] - t[q] : 0u);
-                            can_r |= s[q] < t[q];
+                            le &= s[q] <= thr[q];
+                            lt |= s[q] < t[q];
                         }
                     }
-                    n_checks += 32;
-                    if (pc.pcnt) {
-                        // per-partition split: rows of the target's partition, and the others
-                        const uint32_t pt = __ldg(pc.pid + i);
-                        const unsigned loc = __popc(__ballot_sync(kFull, __ldg(pc.pid + r0 + lane) == pt));
-                        if (lane == 0 && pt < pc.nparts) {
-                            atomicAdd(pc.pcnt + 2 + 4ull * pt + 1, (unsigned long long)loc);
-                            atomicAdd(pc.pcnt + 2 + 4ull * pt + 3, (unsigned long long)(32 - loc));
+                    if (CNT) {
+                        n_checks += 32;
+                        if (pc.pcnt) {
+                            // per-partition split: rows of the target's partition, and the others
+                            const uint32_t pt = __ldg(pc.pid + i);
+                            const unsigned loc = __popc(__ballot_sync(kFull, __ldg(pc.pid + r0 + lane) == pt));
+                            if (lane == 0 && pt < pc.nparts) {
+                                atomicAdd(pc.pcnt + 2 + 4ull * pt + 1, (unsigned long long)loc);
+                                atomicAdd(pc.pcnt + 2 + 4ull * pt + 3, (unsigned long long)(32 - loc));
+                            }
                         }
                     }
                     // rows taken in tile order; best only shrinks, so a row is skipped once
                     // its excess reaches the current delta[best - 1]
-                    unsigned elig = __ballot_sync(kFull, can_r && e_r < wl);
+                    unsigned elig = __ballot_sync(kFull, le & lt);
                     while (elig) {
                         const int c = __ffs(elig) - 1;
                         elig &= elig - 1;
-                        const uint32_t ec = __shfl_sync(kFull, e_r, c);
+                        uint32_t cv[D];   // the row, read by every lane (broadcast), and its excess
+                        ld_cand<D, RES>(cand, r0 + c, cv);
+                        uint32_t ec = 0;
+                        #pragma unroll
+                        for (int q = 0; q < D; q++) ec = max(ec, cv[q] > t[q] ? cv[q] - t[q] : 0u);
                         if (ec >= wl) continue;
-                        uint32_t cv[D];   // the row, read by every lane (broadcast)
-                        if (RES) ld_row<D>(cand, r0 + c, cv); else ldg_row<D>(cand, r0 + c, cv);
                         // first slot holding a width wider than ec
                         const int jlo = __popc(__ballot_sync(kFull, slot_top <= ec));
                         const int jhi = (best - 1) >> 5;
@@ -866,23 +892,26 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                                 }
                                 cj = j;
                             }
-                            bool le = true, lt = false;
+                            bool dle = true, dlt = false;
                             #pragma unroll
                             for (int q = 0; q < D; q++) {
-                                le &= cv[q] <= chi[q];
-                                lt |= cv[q] < clo[q];
+                                dle &= cv[q] <= chi[q];
+                                dlt |= cv[q] < clo[q];
                             }
-                            n_tests += 32;
-                            if (pc.pcnt && lane == 0 && __ldg(pc.pid + i) < pc.nparts) {
-                                const uint32_t pt = __ldg(pc.pid + i);
-                                atomicAdd(pc.pcnt + 2 + 4ull * pt + (__ldg(pc.pid + r0 + c) == pt ? 0 : 2), 32ull);
+                            if (CNT) {
+                                n_tests += 32;
+                                if (pc.pcnt && lane == 0 && __ldg(pc.pid + i) < pc.nparts) {
+                                    const uint32_t pt = __ldg(pc.pid + i);
+                                    atomicAdd(pc.pcnt + 2 + 4ull * pt + (__ldg(pc.pid + r0 + c) == pt ? 0 : 2), 32ull);
+                                }
                             }
-                            const unsigned msk = __ballot_sync(kFull, le & lt);
+                            const unsigned msk = __ballot_sync(kFull, dle & dlt);
                             if (msk) {
                                 best = min(best, 32 * j + __ffs(msk) - 1);
                                 if (best > 0) {
                                     wl = wsteps[best - 1];
-                                    wlq = min(wl >> qshift, 0x7FFFFFFu);
+                                    wlq = min((wl - 1u) >> qshift, 0x7FFFFFFu);
+                                    excess_bounds<D>(t, wl, thr);
                                 }
                                 break;
                             }
@@ -900,7 +929,7 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
     return result;
 }
 
-template <int D, int SLOTS, bool GM>
+template <int D, int SLOTS, bool GM, bool CNT>
 __global__ void __launch_bounds__(dom_threads<D, SLOTS, GM>(), 1)
 k_dominance(DomArgs a) {
     constexpr int DP = padded_dims(D);
@@ -934,8 +963,9 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            const int r = dom_target<D, SLOTS, true, GM>(a.q, stage, stage + cand_words, stage + cand_words + T * DP, T,
-                                                     i, wsteps, n_tests, n_checks, a.pc);
+            const int r = dom_target<D, SLOTS, true, GM, CNT>(a.q, stage, stage + cand_words,
+                                                              stage + cand_words + T * DP, T, i, wsteps, n_tests,
+                                                              n_checks, a.pc);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
     } else {
@@ -944,12 +974,12 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            const int r = dom_target<D, SLOTS, false, GM>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps, n_tests,
-                                                      n_checks, a.pc);
+            const int r = dom_target<D, SLOTS, false, GM, CNT>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps,
+                                                               n_tests, n_checks, a.pc);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
     }
-    if (a.tests && lane == 0 && (n_tests | n_checks)) {
+    if (CNT && a.tests && lane == 0 && (n_tests | n_checks)) {
         atomicAdd(a.tests, n_tests);
         atomicAdd(a.tests + 1, n_checks);
     }
@@ -1000,8 +1030,8 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
         const long long T = (S + kTileRows - 1) / kTileRows;
         const unsigned local = (unsigned)(g - first[lo]);
         const unsigned i = q.iperm ? __ldg(q.iperm + q.t0 + local) : local;
-        const int r = dom_target<D, SLOTS, false, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
-                                                             n_checks, PartCount());
+        const int r = dom_target<D, SLOTS, false, false, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
+                                                                    n_checks, PartCount());
         if (lane == 0) q.out[q.iperm ? local : q.perm[i]] = r;
     }
 }
@@ -1050,19 +1080,24 @@ cudaError_t device_props() {
     return cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 }
 
-template <int D, int SLOTS, bool GM>
+template <int D, int SLOTS, bool GM, bool CNT>
 cudaError_t launch_dom(DomArgs a, cudaStream_t st) {
     static bool configured = false;
     const int smem = g_smem_optin;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_dominance<D, SLOTS, GM>,
+        cudaError_t e = cudaFuncSetAttribute(k_dominance<D, SLOTS, GM, CNT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     a.smem_words = smem / 4;
-    k_dominance<D, SLOTS, GM><<<g_sm_count, dom_threads<D, SLOTS, GM>(), smem, st>>>(a); note_launch();
+    k_dominance<D, SLOTS, GM, CNT><<<g_sm_count, dom_threads<D, SLOTS, GM>(), smem, st>>>(a); note_launch();
     return cudaGetLastError();
+}
+
+template <int D, int SLOTS, bool GM>
+cudaError_t launch_dom_counted(DomArgs a, cudaStream_t st) {
+    return a.tests ? launch_dom<D, SLOTS, GM, true>(a, st) : launch_dom<D, SLOTS, GM, false>(a, st);
 }
 
 template <int D, int SLOTS>
@@ -1142,8 +1177,8 @@ cudaError_t dominance_d(int slots, const DomQuery &q, unsigned *counter, unsigne
     a.counter = counter;
     a.tests = tests;
     a.smem_words = 0;
-    if (q.gbits) return slots == 4 ? launch_dom<D, 4, true>(a, st) : launch_dom<D, 8, true>(a, st);
-    return slots == 4 ? launch_dom<D, 4, false>(a, st) : launch_dom<D, 8, false>(a, st);
+    if (q.gbits) return slots == 4 ? launch_dom_counted<D, 4, true>(a, st) : launch_dom_counted<D, 8, true>(a, st);
+    return slots == 4 ? launch_dom_counted<D, 4, false>(a, st) : launch_dom_counted<D, 8, false>(a, st);
 }
 
 template <int D>
