@@ -35,9 +35,10 @@ namespace gres {
 
 namespace {
 
-constexpr int kCT = 256;            // threads per compaction / filter block
-constexpr int kPer = 2;             // items per thread
-constexpr int kCB = kCT * kPer;     // items per compaction block
+constexpr int kCT = 256;            // threads per compaction block
+constexpr int kPer = 32;            // consecutive rows per compaction thread
+constexpr int kCB = kCT * kPer;     // rows per compaction block (and per k_final segment count)
+static_assert(kCB <= 65536, "row offsets inside a compaction block are 16-bit");
 constexpr int kTriThreads = 256;
 
 template <int D>
@@ -921,22 +922,41 @@ k_compact_sky(const uint32_t *data, int dir, long long n, const uint32_t *skyfla
         run = tb;
         if (blockIdx.x == 0 && threadIdx.x == 0) h->n_sky = ta;
     }
+    // thread t reads the flags of rows [p0, p0 + kPer) (all loads at once); one scan of
+    // the per-thread counts lists the block's skyline rows in order in shared memory,
+    // then the block copies them, one row per thread
+    __shared__ uint16_t lst[kCB];
     const long long b0 = (long long)blockIdx.x * kCB;
-    #pragma unroll 1
-    for (int r = 0; r < kPer; r++) {
-        const long long p = b0 + r * kCT + threadIdx.x;
-        const uint32_t f = p < n ? skyflag[p] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_scan(f, &tot);
-        if (f) {
-            sky_idx[run + ex] = p;
-            uint32_t x[D];
-            load_canon<D>(data, p, dir, x);
-            store_row<D>(sky_rows, run + ex, x);
-            #pragma unroll
-            for (int q = 0; q < D; q++) { lo[q] = min(lo[q], x[q]); hi[q] = max(hi[q], x[q]); }
+    const long long p0 = b0 + (long long)threadIdx.x * kPer;
+    uint32_t f[kPer];
+    if (p0 + kPer <= n && (reinterpret_cast<uintptr_t>(skyflag) & 15u) == 0) {
+        const uint4 *fp = reinterpret_cast<const uint4 *>(skyflag + p0);
+        #pragma unroll
+        for (int k = 0; k < kPer / 4; k++) {
+            const uint4 v = fp[k];
+            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
         }
-        run += tot;
+    } else {
+        #pragma unroll
+        for (int k = 0; k < kPer; k++) f[k] = p0 + k < n ? skyflag[p0 + k] : 0u;
+    }
+    uint32_t c = 0;
+    #pragma unroll
+    for (int k = 0; k < kPer; k++) c += f[k] ? 1u : 0u;
+    uint32_t tot;
+    uint32_t e = block_scan(c, &tot);
+    #pragma unroll
+    for (int k = 0; k < kPer; k++)
+        if (f[k]) lst[e++] = (uint16_t)(threadIdx.x * kPer + k);
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < tot; j += kCT) {
+        const long long p = b0 + lst[j];
+        sky_idx[run + j] = p;
+        uint32_t x[D];
+        load_canon<D>(data, p, dir, x);
+        store_row<D>(sky_rows, run + j, x);
+        #pragma unroll
+        for (int q = 0; q < D; q++) { lo[q] = min(lo[q], x[q]); hi[q] = max(hi[q], x[q]); }
     }
     #pragma unroll
     for (int q = 0; q < D; q++) {
