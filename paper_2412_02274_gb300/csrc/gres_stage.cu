@@ -1025,7 +1025,9 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
             const int mid = (lo + hi + 1) >> 1;
             if (first[mid] <= g) lo = mid; else hi = mid - 1;
         }
-        const DomQuery &q = b.q[lo];
+        // a copy: the search reads its fields often, and indexed reads of the
+        // launch parameters go through the constant cache, shared by all queries
+        const DomQuery q = b.q[lo];
         const long long S = *q.n_sky;
         const long long T = (S + kTileRows - 1) / kTileRows;
         const unsigned local = (unsigned)(g - first[lo]);
