@@ -730,8 +730,10 @@ __device__ __forceinline__ void excess_bounds(const uint32_t (&t)[D], uint32_t w
 // warp; every lane returns it): the first step at which some candidate's
 // projection dominates the target's projection, else K. CNT: count the
 // lane-tests and pruning checks (GRES_FLAG_COUNT_TESTS / _PARTS); the search
-// is the same either way.
-template <int D, int SLOTS, bool RES, bool GM, bool CNT>
+// is the same either way. PAIR: load the rows of the next tile in key order
+// together with the current tile's (the same tiles are looked at, in the same
+// order; it needs D more registers).
+template <int D, int SLOTS, bool RES, bool GM, bool CNT, bool PAIR>
 __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *cand, const uint32_t *tmin,
                                            const uint32_t *smin, long long T, unsigned i, uint32_t *wsteps,
                                            unsigned long long &n_tests, unsigned long long &n_checks,
@@ -827,26 +829,18 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                     }
                 }
                 if (CNT) n_checks += 32;
-                for (;;) {
-                    const uint32_t tk = __reduce_min_sync(kFull, tkey);
-                    if (tk == kNoTile || (tk >> 5) > wlq) break;   // every tile left is too far
-                    const int tl = (int)(tk & 31u);
-                    if (lane == tl) tkey = kNoTile;
-                    if (qshift && (tk >> 5) == wlq && __shfl_sync(kFull, tex, tl) >= wl) continue;
-                    const long long r0 = (sup * 32 + tl) * kTileRows;
+                // The rows of one tile (s: this lane's row, r0: the tile's first row) against
+                // the target; tests the rows that can matter and updates best.
+                auto row_look = [&](const uint32_t (&s)[D], long long r0) {
                     // row level: lane r looks at row r of the tile; a row can dominate t
                     // only if some attribute is below t's and its excess is below wl (every
                     // attribute within the excess bounds): only a width wider than the
                     // excess, and before best, can make it dominate
                     bool le = true, lt = false;
-                    {
-                        uint32_t s[D];
-                        ld_cand<D, RES>(cand, r0 + lane, s);
-                        #pragma unroll
-                        for (int q = 0; q < D; q++) {
-                            le &= s[q] <= thr[q];
-                            lt |= s[q] < t[q];
-                        }
+                    #pragma unroll
+                    for (int q = 0; q < D; q++) {
+                        le &= s[q] <= thr[q];
+                        lt |= s[q] < t[q];
                     }
                     if (CNT) {
                         n_checks += 32;
@@ -918,6 +912,37 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
                         }
                         if (best == 0) break;
                     }
+                };
+                for (;;) {
+                    const uint32_t tk = __reduce_min_sync(kFull, tkey);
+                    if (tk == kNoTile || (tk >> 5) > wlq) break;   // every tile left is too far
+                    const int tl = (int)(tk & 31u);
+                    if (lane == tl) tkey = kNoTile;
+                    if (qshift && (tk >> 5) == wlq && __shfl_sync(kFull, tex, tl) >= wl) continue;
+                    const long long r0 = (sup * 32 + tl) * kTileRows;
+                    uint32_t s[D];
+                    if (!PAIR) {
+                        ld_cand<D, RES>(cand, r0 + lane, s);
+                        row_look(s, r0);
+                        if (best == 0) break;
+                        continue;
+                    }
+                    // PAIR: the tile the search takes next (the keys only lose entries) is
+                    // popped now, so that both tiles' rows load together; it is looked at
+                    // after this one only if it still can matter then
+                    const uint32_t tk2 = __reduce_min_sync(kFull, tkey);
+                    const bool have2 = tk2 != kNoTile && (tk2 >> 5) <= wlq;
+                    const int tl2 = (int)(tk2 & 31u);
+                    if (have2 && lane == tl2) tkey = kNoTile;
+                    const long long r02 = (sup * 32 + tl2) * kTileRows;
+                    uint32_t s2[D];
+                    ld_cand<D, RES>(cand, r0 + lane, s);
+                    if (have2) ld_cand<D, RES>(cand, r02 + lane, s2);
+                    row_look(s, r0);
+                    if (best == 0 || !have2) break;
+                    if ((tk2 >> 5) > wlq) break;   // best moved: every tile left is too far
+                    if (qshift && (tk2 >> 5) == wlq && __shfl_sync(kFull, tex, tl2) >= wl) continue;
+                    row_look(s2, r02);
                     if (best == 0) break;
                 }
                 if (best == 0) break;
@@ -928,6 +953,12 @@ __device__ __forceinline__ int dom_target(const DomQuery &qy, const uint32_t *ca
     }
     return result;
 }
+
+// Tile pairs in the single-query kernel up to d = 6: above that (and in the
+// batched kernel, which holds its query's descriptor too) the extra row does
+// not fit in the 64 registers and spills.
+template <int D>
+constexpr bool kPairTiles = D <= 6;
 
 template <int D, int SLOTS, bool GM, bool CNT>
 __global__ void __launch_bounds__(dom_threads<D, SLOTS, GM>(), 1)
@@ -963,7 +994,7 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            const int r = dom_target<D, SLOTS, true, GM, CNT>(a.q, stage, stage + cand_words,
+            const int r = dom_target<D, SLOTS, true, GM, CNT, kPairTiles<D>>(a.q, stage, stage + cand_words,
                                                               stage + cand_words + T * DP, T, i, wsteps, n_tests,
                                                               n_checks, a.pc);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
@@ -974,7 +1005,7 @@ k_dominance(DomArgs a) {
             if (lane == 0) i = atomicAdd(a.counter, 1u);
             i = __shfl_sync(kFull, i, 0);
             if ((long long)i >= S) break;
-            const int r = dom_target<D, SLOTS, false, GM, CNT>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps,
+            const int r = dom_target<D, SLOTS, false, GM, CNT, kPairTiles<D>>(a.q, a.q.cand, a.q.tmin, a.q.smin, T, i, wsteps,
                                                                n_tests, n_checks, a.pc);
             if (lane == 0) a.q.out[a.q.perm[i]] = r;
         }
@@ -1032,7 +1063,7 @@ k_dominance_batch(const __grid_constant__ DomBatch b) {
         const long long T = (S + kTileRows - 1) / kTileRows;
         const unsigned local = (unsigned)(g - first[lo]);
         const unsigned i = q.iperm ? __ldg(q.iperm + q.t0 + local) : local;
-        const int r = dom_target<D, SLOTS, false, false, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
+        const int r = dom_target<D, SLOTS, false, false, false, false>(q, q.cand, q.tmin, q.smin, T, i, wsteps, n_tests,
                                                                     n_checks, PartCount());
         if (lane == 0) q.out[q.iperm ? local : q.perm[i]] = r;
     }
